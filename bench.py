@@ -1,0 +1,396 @@
+"""Benchmark of the fused compressible-Euler step on GB300.
+
+Default workload: 3D single-fluid Rayleigh-Taylor, 256^3 cells on
+[0,1]x[0,1]x[0,2], FP64, periodic x/y, reflecting z, g = -1, seeded
+multimode perturbation; a bench step is one full time step (one fused
+kernel launch) of the whole grid.  Metric: zone-updates/s (cells x steps /
+s), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+One JSON line is printed by rank 0.  Under torchrun (N > 1) each rank runs
+an independent replica on its own GPU (the update does not shard across
+GPUs here), timing is max over ranks, and value = all ranks' zone-updates /
+that time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1510_05061_gb300 import inputs  # noqa: E402
+
+METRIC = "zone-updates/s"
+UNIT = "zone-updates/s"
+
+# Algorithmic work per zone-update of the fused 3D step:
+# bytes = read U^n once + write U^{n+1} once = 2 * nvar * sizeof(T);
+# FP64 operations counted once per cell and once per face (three faces per
+# cell), divisions and square roots counted as one operation each.
+FLOPS_PER_ZONE_3D = 612
+FLOPS_PER_ZONE_2D = 350
+
+CONFIGS = {
+    # name: (builder, description, precision, hse)
+    "rt256-fp64": dict(n=256, precision=inputs.FP64, hse=0,
+                       desc="3D single-fluid Rayleigh-Taylor 256^3 FP64 (g=-1, modes 4-16, amp 0.01), 200-step run"),
+    "rt256-fp64-hse": dict(n=256, precision=inputs.FP64, hse=1,
+                           desc="3D Rayleigh-Taylor 256^3 FP64 with hydrostatic-background subtraction"),
+    "rt512-fp32": dict(n=512, precision=inputs.FP32, hse=1,
+                       desc="3D Rayleigh-Taylor 512^3 FP32 bulk, FP64 dt/totals/background subtraction"),
+    "rt256-fp32": dict(n=256, precision=inputs.FP32, hse=1,
+                       desc="3D Rayleigh-Taylor 256^3 FP32 bulk with hydrostatic-background subtraction"),
+}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    """Dense FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk
+    x 2 flop x clock (1.26 TFLOP/s at 2070 MHz, the part's nominal figure)."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_workload(cfg):
+    c = CONFIGS[cfg]
+    prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
+    return prob, W, c
+
+
+# --------------------------------------------------------------- oracle
+def oracle_sample(seconds: float = 12.0, max_steps: int = 4, cfg="rt256-fp64", nz_slab=None):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the
+    workload.  Returns (zone-updates/s, cores, sample description)."""
+    import oracle
+
+    oracle.build()
+    prob, W, c = build_workload(cfg)
+    desc = f"{c['n']}^3 full grid"
+    if nz_slab is not None:
+        # a slab of nz_slab planes around the interface, same x-y extent
+        k0 = prob.n[2] // 2 - nz_slab // 2
+        z_lo = prob.lo[2] + k0 * prob.dx()[2]
+        z_hi = z_lo + nz_slab * prob.dx()[2]
+        kw = dict(n=(prob.n[0], prob.n[1], nz_slab), lo=(0.0, 0.0, z_lo), hi=(1.0, 1.0, z_hi))
+        if prob.hse_subtract:
+            kw.update(bg_rho_c=prob.bg_rho_c[k0:k0 + nz_slab + 4], bg_p_c=prob.bg_p_c[k0:k0 + nz_slab + 4],
+                      bg_rho_f=prob.bg_rho_f[k0:k0 + nz_slab + 5], bg_p_f=prob.bg_p_f[k0:k0 + nz_slab + 5])
+        prob = prob.replace(**kw)
+        W = np.ascontiguousarray(W[:, k0:k0 + nz_slab])
+        desc = f"{prob.n[0]}x{prob.n[1]}x{nz_slab} slab of the {c['n']}^3 initial state around the interface"
+    o = oracle.Oracle(prob)
+    U = o.state_from_prim(W)
+    cores = o.L.orc_max_threads()
+    done, t0 = 0, time.perf_counter()
+    while done < max_steps:
+        U, _, s, _ = o.run(U, max_steps=1)
+        done += s
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return prob.ncell * done / el, cores, f"{desc}, {done} oracle step(s), {el:.1f} s"
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    cfg = args.config
+    prob, W, c = build_workload(cfg)
+    import oracle
+
+    oracle.build()
+    nz_slab = 16
+    k0 = prob.n[2] // 2 - nz_slab // 2
+    sprob = prob.replace(n=(prob.n[0], prob.n[1], nz_slab),
+                         lo=(0.0, 0.0, prob.lo[2] + k0 * prob.dx()[2]),
+                         hi=(1.0, 1.0, prob.lo[2] + (k0 + nz_slab) * prob.dx()[2]))
+    if prob.hse_subtract:
+        sprob = sprob.replace(bg_rho_c=prob.bg_rho_c[k0:k0 + nz_slab + 4], bg_p_c=prob.bg_p_c[k0:k0 + nz_slab + 4],
+                              bg_rho_f=prob.bg_rho_f[k0:k0 + nz_slab + 5], bg_p_f=prob.bg_p_f[k0:k0 + nz_slab + 5])
+    Ws = np.ascontiguousarray(W[:, k0:k0 + nz_slab])
+    o = oracle.Oracle(sprob)
+    U = o.state_from_prim(Ws)
+    for _ in range(args.warmup):
+        U, _, _, _ = o.run(U, max_steps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _, _, _ = o.run(U, max_steps=1)
+    el = time.perf_counter() - t0
+    value = sprob.ncell * args.steps / el
+    cores = o.L.orc_max_threads()
+    sample = (f"{sprob.n[0]}x{sprob.n[1]}x{nz_slab} slab of the {c['n']}^3 Rayleigh-Taylor initial state "
+              f"around the interface; one FP64 oracle step per bench step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": c["desc"], "grid": list(prob.n), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_1510_05061_gb300 import build as hbuild
+    from paper_1510_05061_gb300 import hydro
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hydro.load()
+    prob, W, c = build_workload(args.config)
+    N = prob.ncell
+    itemsize = 4 if prob.precision == inputs.FP32 else 8
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident run: inputs in HBM before the timed region
+    sim = hydro.Simulation(prob, W, stream=stream)
+    for _ in range(args.warmup):
+        sim.step()
+    torch.cuda.synchronize()
+    nlaunch0 = sim.launches()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_all0.record(stream)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            sim.step()
+            ends[i].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = sim.launches() - nlaunch0
+    el_ms = t_all0.elapsed_time(t_all1)
+    el_ms = max_over_ranks(world, el_ms)
+    kern_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    t_sim = sim.t
+    ok = np.isfinite(t_sim)
+    sim.close()
+    del sim
+
+    value = world * N * args.steps / (el_ms * 1e-3)
+
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        W_pin = torch.empty(W.shape, dtype=torch.float64, pin_memory=True)
+        W_pin.numpy()[...] = W
+        out_pin = torch.empty(prob.shape, dtype=torch.float32 if itemsize == 4 else torch.float64,
+                              pin_memory=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = hydro.Simulation(prob, W_pin.numpy(), stream=stream)
+        for _ in range(args.steps):
+            sim2.step()
+        hydro.hydro_get_state(sim2.h, out_pin.numpy())
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        sim2.close()
+        e2e = {"value": world * N * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(W.nbytes / args.steps),
+               "d2h_bytes_per_step": int(N * prob.nvar * itemsize / args.steps),
+               "note": "hydro_init from pinned host primitives + K steps + hydro_get_state to pinned host"}
+
+    # ---- roofline of the step kernel
+    peaks, peak_kind = measured_peaks()
+    bytes_per_zone = 2 * prob.nvar * itemsize
+    zones_per_launch = N
+    achieved_gbs = bytes_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    clocks = clk.summary()
+    if prob.precision == inputs.FP64:
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_tf = fp64_peak_tflops(sm_mhz)
+        ach_tf = FLOPS_PER_ZONE_3D * zones_per_launch / (kern_avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": ach_tf / peak_tf, "traffic": args.traffic,
+                    "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                    "kernel": "step3d_kernel<double>",
+                    "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind}}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm_peak, "traffic": args.traffic,
+                    "peak_kind": peak_kind, "kernel": "step3d_kernel<float>"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_sample(cfg=args.config, nz_slab=32)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if itemsize == 4 else "f64", "data": "synthetic",
+            "config": {"workload": c["desc"], "grid": list(prob.n), "precision": "fp32" if itemsize == 4 else "fp64",
+                       "hse_subtract": prob.hse_subtract, "state_bytes": N * prob.nvar * itemsize,
+                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (N * prob.nvar * itemsize / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "kernel_ms_avg": kern_avg_ms,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "t_sim": t_sim if ok else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="rt256-fp64", choices=sorted(CONFIGS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the step kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

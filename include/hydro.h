@@ -1,0 +1,159 @@
+/*
+ * hydro.h -- C ABI of libhydro, a GB300 (sm_103a) library that advances the
+ * compressible Euler equations of a gamma-law gas with a constant-gravity
+ * source on a uniform Cartesian grid.
+ *
+ * The paper this library serves ("Modeling Astrophysical Explosions with
+ * Sustained Exascale Computing", introduction) describes the star as a fluid
+ * on a domain-decomposed Cartesian grid, and ("Capabilities needed") says
+ * that every time step needs nearest-neighbour communication plus a global
+ * one.  Here the nearest-neighbour part is the depth-2 stencil halo read
+ * inside one GPU and the global part is the CFL time-step min-reduction and
+ * the conserved-total sums.  The paper prints no scheme; the update is the
+ * unsplit finite-volume step:
+ *   - primitive variables W = (rho, u_0 .. u_{ndim-1}, p), p = (gamma-1)(E - |m|^2/(2 rho));
+ *   - PLM slopes with the MC limiter (van Leer 1977);
+ *   - single-stage unsplit MUSCL-Hancock half step in primitive variables
+ *     (Toro, "Riemann Solvers and Numerical Methods for Fluid Dynamics",
+ *     3rd ed., sec. 14.4), all axes and gravity at once; a cell whose
+ *     predicted face density or pressure is not positive uses zero slopes;
+ *   - an HLLC flux at every face (Toro sec. 10.4-10.6, Davis wave speeds);
+ *   - conservative update: density first, momentum source g (rho^n +
+ *     rho^{n+1})/2, energy source g . (low-face + high-face mass flux)/2;
+ *   - dt = cfl / max_cells sum_d (|u_d| + c)/dx_d in FP64, taken from the
+ *     state each step starts from, clamped to land exactly on a target time.
+ * Boundaries: outflow (zero gradient), periodic, reflecting (mirror with the
+ * normal momentum negated; the far side of a wall face is the mirror of the
+ * near side's predicted state, so no mass crosses a wall).
+ *
+ * Memory and ownership.  The caller owns all device memory and the stream:
+ * two state buffers (ping-pong) of hydro_state_bytes() each and one workspace
+ * of hydro_workspace_bytes(), all device pointers with 256-byte alignment.
+ * The library allocates no device memory; it owns only the host-side handle.
+ * A state is nvar = ndim + 2 planes of nx*ny*nz values, plane q at offset
+ * q*nx*ny*nz, x fastest: (rho, rho u_0 .. rho u_{ndim-1}, E), in FP64, or in
+ * FP32 for HYDRO_FP32.  With hse_subtract the stored state is the
+ * perturbation U - U0(z) from the hydrostatic background U0 = (rho0, 0, 0, 0,
+ * p0/(gamma-1)).
+ *
+ * Errors.  Every call returns a hydro_status; nothing traps, exits or throws
+ * across the ABI.  CUDA failures are reported as HYDRO_ERR_CUDA.  Device-side
+ * detection of a non-positive or non-finite density or pressure puts the
+ * handle in an error state (further steps leave the state unchanged) that is
+ * reported as HYDRO_ERR_NONPHYSICAL by the next call that synchronises, until
+ * hydro_set_state or hydro_destroy.  One host thread per handle.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYDRO_OK = 0,
+    HYDRO_ERR_INVALID_ARG = -1,   /* bad pointer, size, enum or alignment */
+    HYDRO_ERR_OOM = -2,           /* a caller buffer is too small */
+    HYDRO_ERR_CUDA = -3,          /* a CUDA call failed */
+    HYDRO_ERR_NONPHYSICAL = -4,   /* rho or p <= 0 or non-finite was produced */
+    HYDRO_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+    HYDRO_ERR_STATE = -6          /* call not valid in the handle's state */
+} hydro_status;
+
+enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1, HYDRO_BC_REFLECT = 2 };
+enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1 /* FP32 state and update, FP64 dt, time and totals */ };
+enum {
+    HYDRO_RED_TOTALS = 1,    /* out[nvar]: sum over cells of (rho, m_d, E) * cell volume, FP64, fixed order */
+    HYDRO_RED_DT = 2,        /* out[1]: CFL dt of the current state */
+    HYDRO_RED_TIME = 3,      /* out[1]: current time */
+    HYDRO_RED_MAXSPEED = 4,  /* out[1]: max_cells sum_d (|u_d| + c)/dx_d of the current state */
+    HYDRO_RED_STEP = 5,      /* out[1]: steps taken since init or set_state */
+    HYDRO_RED_DT_LAST = 6    /* out[1]: dt taken by the last step */
+};
+
+/* Problem description.  ndim 2 or 3; n[d] >= 2 for d < ndim and n[d] == 1
+   for d >= ndim; lo < hi; bc_* per axis; gamma > 1; cfl > 0; grav is the
+   constant acceleration.  hse_subtract = 1 needs ndim = 3 and gravity along
+   z only, and the background tables of hydro_init. */
+typedef struct {
+    int ndim;
+    int n[3];
+    double lo[3], hi[3];
+    int bc_lo[3], bc_hi[3];
+    double gamma, cfl;
+    double grav[3];
+    int precision;       /* HYDRO_FP64 or HYDRO_FP32 */
+    int hse_subtract;
+} hydro_problem;
+
+typedef struct hydro_sim hydro_sim;
+
+/* Bytes of one state buffer: nvar * nx*ny*nz * (8 or 4).  0 if invalid. */
+size_t hydro_state_bytes(const hydro_problem *prob);
+
+/* Bytes of the workspace: time-control block, per-CTA partials, FP64
+   background tables.  0 if invalid. */
+size_t hydro_workspace_bytes(const hydro_problem *prob);
+
+/* Bind caller buffers and set the initial state.
+   Ua, Ub: device state buffers (hydro_state_bytes each); work: device
+   workspace (hydro_workspace_bytes).  W0: HOST array of total primitive
+   variables (rho, u_0 .. u_{ndim-1}, p), FP64, nvar planes, converted to the
+   stored form on the device (Ub is used as staging).  bg: HOST FP64
+   background tables when hse_subtract (else NULL): rho0 and p0 at the
+   centres of planes k = -2 .. nz+1 (2 arrays of nz+4, in that order), then
+   rho0 and p0 at the faces z_lo + f dz, f = -2 .. nz+2 (2 arrays of nz+5).
+   stream: a cudaStream_t (NULL = legacy default stream).  Computes the
+   first dt on the device; t = 0, step = 0.  *out receives the handle. */
+int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work,
+               const double *W0, const double *bg, void *stream, hydro_sim **out);
+
+/* One step on the handle's stream.  dt_taken (nullable): when given, the
+   call synchronises and returns the dt used; when NULL nothing is read back
+   and errors surface at the next synchronising call. */
+int hydro_step(hydro_sim *sim, double *dt_taken);
+
+/* Steps until t reaches t_end exactly (the last dt is clamped) or max_steps
+   steps have been taken.  Reads the device time block once per batch of
+   launches.  nsteps_out, t_out nullable. */
+int hydro_advance_to(hydro_sim *sim, double t_end, long max_steps, long *nsteps_out,
+                     double *t_out);
+
+/* Reductions of the current state (see HYDRO_RED_*); synchronises. */
+int hydro_reduce(hydro_sim *sim, int what, double *out);
+
+/* Device pointer of the buffer that holds the current state. */
+void *hydro_current(hydro_sim *sim);
+
+/* Raw stored state (hydro_state_bytes) to / from HOST memory, for
+   checkpoint and restart.  set_state also sets t and step, recomputes dt and
+   clears the error state. */
+int hydro_get_state(hydro_sim *sim, void *host_dst);
+int hydro_set_state(hydro_sim *sim, const void *host_src, double t, long step);
+
+/* Current state as FP64 total conserved variables (what = 0) or total
+   primitive variables (what = 1) into a HOST array of nvar*N doubles; the
+   spare ping-pong buffer is used as device staging. */
+int hydro_get_fields(hydro_sim *sim, int what, double *host_dst);
+
+/* Test hook: overwrite one stored value of the current state with v
+   (converted to the stored precision).  Used to inject a non-physical cell
+   from the host. */
+int hydro_debug_poke(hydro_sim *sim, int var, long cell, double v);
+
+/* Select the 3D z-chunk length (planes per CTA); 0 restores the default. */
+int hydro_set_zchunk(hydro_sim *sim, int zchunk);
+
+/* Number of kernels launched by this handle so far. */
+long hydro_launch_count(hydro_sim *sim);
+
+int hydro_destroy(hydro_sim *sim);
+const char *hydro_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

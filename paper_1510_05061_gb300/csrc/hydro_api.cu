@@ -1,0 +1,494 @@
+// hydro_api.cu -- the C ABI declared in include/hydro.h: argument checking,
+// workspace layout, launch configuration and host-side time control.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hydro.h"
+#include "hydro_internal.h"
+#include "launchers.h"
+
+using namespace hydro;
+
+struct hydro_sim {
+    hydro_problem prob;
+    int nvar;
+    long long N, plane;
+    size_t state_bytes;
+    void *buf[2];
+    int cur;                 // index of the buffer holding the current state
+    unsigned char *work;
+    WorkLayout lay;
+    Ctrl *ctrl;
+    double *partial;
+    PlaneBG *bg;
+    cudaStream_t stream;
+    double dx[3], inv_dx[3], cell_volume;
+    int tiles_x, tiles_y;
+    int zchunk;
+    long launches;
+    int err_state;           // sticky host-side copy of a non-physical error
+    std::vector<PlaneBG> bg_host;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool aligned(const void *p) { return (reinterpret_cast<uintptr_t>(p) % ALIGN) == 0; }
+
+int check_problem(const hydro_problem *p)
+{
+    if (!p) return HYDRO_ERR_INVALID_ARG;
+    if (p->ndim != 2 && p->ndim != 3) return HYDRO_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d) {
+        if (d < p->ndim) {
+            if (p->n[d] < 2) return HYDRO_ERR_INVALID_ARG;
+        } else if (p->n[d] != 1) {
+            return HYDRO_ERR_INVALID_ARG;
+        }
+        if (!(p->hi[d] > p->lo[d]) || !std::isfinite(p->hi[d] - p->lo[d])) return HYDRO_ERR_INVALID_ARG;
+        if (p->bc_lo[d] < 0 || p->bc_lo[d] > 2 || p->bc_hi[d] < 0 || p->bc_hi[d] > 2)
+            return HYDRO_ERR_INVALID_ARG;
+        if ((p->bc_lo[d] == HYDRO_BC_PERIODIC) != (p->bc_hi[d] == HYDRO_BC_PERIODIC))
+            return HYDRO_ERR_INVALID_ARG;
+        if (!std::isfinite(p->grav[d])) return HYDRO_ERR_INVALID_ARG;
+    }
+    if (p->ndim == 2 && p->grav[2] != 0.0) return HYDRO_ERR_INVALID_ARG;
+    if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !std::isfinite(p->gamma) || !std::isfinite(p->cfl))
+        return HYDRO_ERR_INVALID_ARG;
+    if (p->precision != HYDRO_FP64 && p->precision != HYDRO_FP32) return HYDRO_ERR_INVALID_ARG;
+    if (p->hse_subtract != 0 && p->hse_subtract != 1) return HYDRO_ERR_INVALID_ARG;
+    if (p->hse_subtract && (p->ndim != 3 || p->grav[0] != 0.0 || p->grav[1] != 0.0))
+        return HYDRO_ERR_INVALID_ARG;
+    // 32-bit plane and cell indexing inside a plane; 64-bit across planes
+    const long long plane = (long long)p->n[0] * p->n[1];
+    if (plane > (1ll << 31) - 1) return HYDRO_ERR_INVALID_ARG;
+    return HYDRO_OK;
+}
+
+int tiles_along(int n, int t) { return (n + t - 1) / t; }
+
+int step_max_ctas(const hydro_problem *p)
+{
+    if (p->ndim == 2)
+        return tiles_along(p->n[0], STEP2D_TX) * tiles_along(p->n[1], STEP2D_TY);
+    // zchunk >= 1: at most nz chunks
+    return tiles_along(p->n[0], STEP3D_TX) * tiles_along(p->n[1], STEP3D_TY) * p->n[2];
+}
+
+WorkLayout layout(const hydro_problem *p)
+{
+    WorkLayout L{};
+    const long long N = (long long)p->n[0] * p->n[1] * p->n[2];
+    const int aux = aux_reduce_blocks(N);
+    const int nparts = std::max(step_max_ctas(p), 5 * aux);
+    L.max_ctas = nparts;
+    size_t off = 0;
+    L.ctrl = off;
+    off = align_up(off + sizeof(Ctrl));
+    L.partial = off;
+    off = align_up(off + sizeof(double) * (size_t)nparts);
+    L.bg = off;
+    off = align_up(off + (p->hse_subtract ? sizeof(PlaneBG) * (size_t)(p->n[2] + 5) : 0));
+    L.red = off;
+    L.total = off;
+    return L;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_CUDA; }
+
+AuxArgs aux_args(const hydro_sim *s, void *U)
+{
+    AuxArgs a{};
+    a.U = U;
+    a.ndim = s->prob.ndim;
+    for (int d = 0; d < 3; ++d) { a.n[d] = s->prob.n[d]; a.inv_dx[d] = s->inv_dx[d]; }
+    a.N = s->N;
+    a.plane = s->plane;
+    a.gamma = s->prob.gamma;
+    a.cfl = s->prob.cfl;
+    a.cell_volume = s->cell_volume;
+    a.ctrl = s->ctrl;
+    a.partial = s->partial;
+    a.bg = s->prob.hse_subtract ? s->bg : nullptr;
+    a.hse = s->prob.hse_subtract;
+    a.fp32 = s->prob.precision == HYDRO_FP32;
+    return a;
+}
+
+int default_zchunk(const hydro_sim *s)
+{
+    if (s->prob.ndim == 2) return 1;
+    const int nz = s->prob.n[2];
+    const long long tiles = (long long)s->tiles_x * s->tiles_y;
+    // aim for >= 8 CTAs per SM on 152 SMs with chunks of 8..64 planes,
+    // split evenly so that no chunk is much shorter than the others
+    long long nch = std::max(1ll, (8ll * 152 + tiles - 1) / tiles);
+    nch = std::max(nch, (long long)((nz + 63) / 64));
+    nch = std::min(nch, std::max(1ll, (long long)(nz / 8)));
+    return (int)((nz + nch - 1) / nch);
+}
+
+StepArgs step_args(const hydro_sim *s, double t_end)
+{
+    StepArgs a{};
+    a.U = s->buf[s->cur];
+    a.Unew = s->buf[1 - s->cur];
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = s->prob.n[d];
+        a.bc_lo[d] = s->prob.bc_lo[d];
+        a.bc_hi[d] = s->prob.bc_hi[d];
+        a.inv_dx[d] = d < s->prob.ndim ? s->inv_dx[d] : 0.0;
+        a.grav[d] = s->prob.grav[d];
+    }
+    a.plane = s->plane;
+    a.vstride = s->N;
+    a.gamma = s->prob.gamma;
+    a.cfl = s->prob.cfl;
+    a.t_end = t_end;
+    a.ctrl = s->ctrl;
+    a.partial = s->partial;
+    a.bg = s->prob.hse_subtract ? s->bg : nullptr;
+    a.zchunk = s->zchunk;
+    a.tiles_x = s->tiles_x;
+    return a;
+}
+
+int launch_step(hydro_sim *s, double t_end)
+{
+    StepArgs a = step_args(s, t_end);
+    cudaError_t e;
+    const bool fp32 = s->prob.precision == HYDRO_FP32;
+    if (s->prob.ndim == 2) {
+        dim3 grid(s->tiles_x * s->tiles_y, 1);
+        e = launch_step2d(a, grid, s->stream, fp32);
+    } else {
+        const int nch = (s->prob.n[2] + s->zchunk - 1) / s->zchunk;
+        dim3 grid(s->tiles_x * s->tiles_y, nch);
+        e = fp32 ? launch_step3d_f32(a, grid, s->stream, s->prob.hse_subtract != 0)
+                 : launch_step3d_f64(a, grid, s->stream, s->prob.hse_subtract != 0);
+    }
+    s->launches += 1;
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    s->cur = 1 - s->cur;
+    return HYDRO_OK;
+}
+
+int read_ctrl(hydro_sim *s, Ctrl *out)
+{
+    cudaError_t e = cudaMemcpyAsync(out, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    if (out->err) s->err_state = 1;
+    return HYDRO_OK;
+}
+
+int recompute_dt(hydro_sim *s)
+{
+    AuxArgs a = aux_args(s, s->buf[s->cur]);
+    s->launches += 1;
+    return cuda_status(launch_signal(a, s->stream));
+}
+
+// Stage a host FP64 array (nvar planes of N) through the spare buffer in
+// chunks; fn(c0, m, staging) is called for each chunk after its upload.
+template <typename F>
+int staged_upload(hydro_sim *s, const double *host, F fn)
+{
+    const long long cap = (long long)(s->state_bytes / (sizeof(double) * s->nvar));
+    double *stg = static_cast<double *>(s->buf[1 - s->cur]);
+    for (long long c0 = 0; c0 < s->N; c0 += cap) {
+        const long long m = std::min(cap, s->N - c0);
+        for (int q = 0; q < s->nvar; ++q) {
+            cudaError_t e = cudaMemcpyAsync(stg + (size_t)q * m, host + (size_t)q * s->N + c0,
+                                            sizeof(double) * m, cudaMemcpyHostToDevice, s->stream);
+            if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+        }
+        int rc = fn(c0, m, stg);
+        if (rc) return rc;
+        // the next chunk's upload must not overwrite staging still being read
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
+    }
+    return HYDRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hydro_state_bytes(const hydro_problem *prob)
+{
+    if (check_problem(prob)) return 0;
+    const size_t N = (size_t)prob->n[0] * prob->n[1] * prob->n[2];
+    return N * (prob->ndim + 2) * (prob->precision == HYDRO_FP32 ? 4 : 8);
+}
+
+size_t hydro_workspace_bytes(const hydro_problem *prob)
+{
+    if (check_problem(prob)) return 0;
+    return layout(prob).total;
+}
+
+int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const double *W0,
+               const double *bg, void *stream, hydro_sim **out)
+{
+    if (!out) return HYDRO_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = check_problem(prob);
+    if (rc) return rc;
+    if (!Ua || !Ub || !work || !W0 || Ua == Ub) return HYDRO_ERR_INVALID_ARG;
+    if (!aligned(Ua) || !aligned(Ub) || !aligned(work)) return HYDRO_ERR_INVALID_ARG;
+    if (prob->hse_subtract && !bg) return HYDRO_ERR_INVALID_ARG;
+
+    hydro_sim *s = new (std::nothrow) hydro_sim();
+    if (!s) return HYDRO_ERR_OOM;
+    s->prob = *prob;
+    s->nvar = prob->ndim + 2;
+    s->plane = (long long)prob->n[0] * prob->n[1];
+    s->N = s->plane * prob->n[2];
+    s->state_bytes = hydro_state_bytes(prob);
+    s->buf[0] = Ua;
+    s->buf[1] = Ub;
+    s->cur = 0;
+    s->work = static_cast<unsigned char *>(work);
+    s->lay = layout(prob);
+    s->ctrl = reinterpret_cast<Ctrl *>(s->work + s->lay.ctrl);
+    s->partial = reinterpret_cast<double *>(s->work + s->lay.partial);
+    s->bg = reinterpret_cast<PlaneBG *>(s->work + s->lay.bg);
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->cell_volume = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        s->dx[d] = (prob->hi[d] - prob->lo[d]) / prob->n[d];
+        s->inv_dx[d] = 1.0 / s->dx[d];
+        if (d < prob->ndim) s->cell_volume *= s->dx[d];
+    }
+    if (prob->ndim == 2) {
+        s->tiles_x = tiles_along(prob->n[0], STEP2D_TX);
+        s->tiles_y = tiles_along(prob->n[1], STEP2D_TY);
+    } else {
+        s->tiles_x = tiles_along(prob->n[0], STEP3D_TX);
+        s->tiles_y = tiles_along(prob->n[1], STEP3D_TY);
+    }
+    s->zchunk = default_zchunk(s);
+
+    cudaError_t e = cudaMemsetAsync(s->work, 0, s->lay.total, s->stream);
+    if (e != cudaSuccess) { delete s; return HYDRO_ERR_CUDA; }
+
+    if (prob->hse_subtract) {
+        // per-plane FP64 background constants for planes -2 .. nz+2
+        const int nz = prob->n[2];
+        const double *rc_ = bg, *pc_ = bg + (nz + 4), *rf_ = bg + 2 * (nz + 4),
+                     *pf_ = bg + 2 * (nz + 4) + (nz + 5);
+        s->bg_host.assign(nz + 5, PlaneBG{});
+        for (int k = -2; k <= nz + 2; ++k) {
+            PlaneBG &b = s->bg_host[k + 2];
+            const bool has_c = k <= nz + 1;
+            b.rho_c = has_c ? rc_[k + 2] : 0.0;
+            b.p_c = has_c ? pc_[k + 2] : 0.0;
+            b.rho_f = rf_[k + 2];
+            b.p_f = pf_[k + 2];
+            if (has_c) {
+                b.drho = rf_[k + 3] - rf_[k + 2];
+                b.dp = pf_[k + 3] - pf_[k + 2];
+                b.B = b.dp / s->dx[2] - b.rho_c * prob->grav[2];
+            }
+            if (!std::isfinite(b.rho_c) || !std::isfinite(b.p_c) || !std::isfinite(b.rho_f) ||
+                !std::isfinite(b.p_f)) {
+                delete s;
+                return HYDRO_ERR_INVALID_ARG;
+            }
+        }
+        e = cudaMemcpyAsync(s->bg, s->bg_host.data(), sizeof(PlaneBG) * s->bg_host.size(),
+                            cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) { delete s; return HYDRO_ERR_CUDA; }
+    }
+
+    AuxArgs a = aux_args(s, s->buf[s->cur]);
+    rc = staged_upload(s, W0, [&](long long c0, long long m, double *stg) {
+        s->launches += 1;
+        return cuda_status(launch_init_convert(a, stg, c0, m, s->stream));
+    });
+    if (rc == HYDRO_OK) rc = recompute_dt(s);
+    Ctrl c;
+    if (rc == HYDRO_OK) rc = read_ctrl(s, &c);
+    if (rc != HYDRO_OK) { delete s; return rc; }
+    *out = s;
+    return c.err ? HYDRO_ERR_NONPHYSICAL : HYDRO_OK;
+}
+
+int hydro_step(hydro_sim *s, double *dt_taken)
+{
+    if (!s) return HYDRO_ERR_INVALID_ARG;
+    if (s->err_state) return HYDRO_ERR_NONPHYSICAL;
+    int rc = launch_step(s, INFINITY);
+    if (rc) return rc;
+    if (dt_taken) {
+        Ctrl c;
+        rc = read_ctrl(s, &c);
+        if (rc) return rc;
+        *dt_taken = c.dt_last;
+        if (c.err) return HYDRO_ERR_NONPHYSICAL;
+    }
+    return HYDRO_OK;
+}
+
+int hydro_advance_to(hydro_sim *s, double t_end, long max_steps, long *nsteps_out, double *t_out)
+{
+    if (!s || !std::isfinite(t_end) || max_steps < 0) return HYDRO_ERR_INVALID_ARG;
+    if (s->err_state) return HYDRO_ERR_NONPHYSICAL;
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    const long long step0 = c.step;
+    long launched = 0;
+    long batch = 4;
+    while (c.t < t_end && c.step - step0 < max_steps && !c.err) {
+        // launch up to `batch` steps, never more than the steps still allowed;
+        // launches after t_end is reached carry the state over unchanged
+        const long allowed = max_steps - (long)(c.step - step0);
+        const long nb = std::min(batch, allowed);
+        for (long i = 0; i < nb; ++i) {
+            rc = launch_step(s, t_end);
+            if (rc) return rc;
+            ++launched;
+        }
+        rc = read_ctrl(s, &c);
+        if (rc) return rc;
+        batch = std::min(batch * 2, 64l);
+        // estimate of the steps still needed keeps the overshoot small
+        if (c.dt_next > 0.0 && c.t < t_end) {
+            const double need = std::ceil((t_end - c.t) / c.dt_next);
+            if (need < batch) batch = std::max(1l, (long)need);
+        }
+    }
+    if (nsteps_out) *nsteps_out = (long)(c.step - step0);
+    if (t_out) *t_out = c.t;
+    return c.err ? HYDRO_ERR_NONPHYSICAL : HYDRO_OK;
+}
+
+int hydro_reduce(hydro_sim *s, int what, double *out)
+{
+    if (!s || !out) return HYDRO_ERR_INVALID_ARG;
+    Ctrl c;
+    int rc;
+    if (what == HYDRO_RED_TOTALS) {
+        AuxArgs a = aux_args(s, s->buf[s->cur]);
+        s->launches += 1;
+        rc = cuda_status(launch_totals(a, s->stream));
+        if (rc) return rc;
+    } else if (what < HYDRO_RED_DT || what > HYDRO_RED_DT_LAST) {
+        return HYDRO_ERR_INVALID_ARG;
+    }
+    rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    switch (what) {
+    case HYDRO_RED_TOTALS: for (int q = 0; q < s->nvar; ++q) out[q] = c.totals[q]; break;
+    case HYDRO_RED_DT: out[0] = c.dt_next; break;
+    case HYDRO_RED_TIME: out[0] = c.t; break;
+    case HYDRO_RED_MAXSPEED: out[0] = c.max_speed; break;
+    case HYDRO_RED_STEP: out[0] = (double)c.step; break;
+    case HYDRO_RED_DT_LAST: out[0] = c.dt_last; break;
+    }
+    return c.err ? HYDRO_ERR_NONPHYSICAL : HYDRO_OK;
+}
+
+void *hydro_current(hydro_sim *s) { return s ? s->buf[s->cur] : nullptr; }
+
+int hydro_get_state(hydro_sim *s, void *host_dst)
+{
+    if (!s || !host_dst) return HYDRO_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(host_dst, s->buf[s->cur], s->state_bytes, cudaMemcpyDeviceToHost,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
+}
+
+int hydro_set_state(hydro_sim *s, const void *host_src, double t, long step)
+{
+    if (!s || !host_src || !std::isfinite(t) || step < 0) return HYDRO_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], host_src, s->state_bytes, cudaMemcpyHostToDevice,
+                                    s->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    Ctrl c{};
+    c.t = t;
+    c.step = step;
+    e = cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    s->err_state = 0;
+    int rc = recompute_dt(s);
+    if (rc) return rc;
+    rc = read_ctrl(s, &c);   // also orders the host copies before return
+    if (rc) return rc;
+    return c.err ? HYDRO_ERR_NONPHYSICAL : HYDRO_OK;
+}
+
+int hydro_get_fields(hydro_sim *s, int what, double *host_dst)
+{
+    if (!s || !host_dst || (what != 0 && what != 1)) return HYDRO_ERR_INVALID_ARG;
+    const long long cap = (long long)(s->state_bytes / (sizeof(double) * s->nvar));
+    double *stg = static_cast<double *>(s->buf[1 - s->cur]);
+    AuxArgs a = aux_args(s, s->buf[s->cur]);
+    for (long long c0 = 0; c0 < s->N; c0 += cap) {
+        const long long m = std::min(cap, s->N - c0);
+        s->launches += 1;
+        cudaError_t e = launch_fields(a, stg, c0, m, what, s->stream);
+        for (int q = 0; q < s->nvar && e == cudaSuccess; ++q)
+            e = cudaMemcpyAsync(host_dst + (size_t)q * s->N + c0, stg + (size_t)q * m,
+                                sizeof(double) * m, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    }
+    return HYDRO_OK;
+}
+
+int hydro_debug_poke(hydro_sim *s, int var, long cell, double v)
+{
+    if (!s || var < 0 || var >= s->nvar || cell < 0 || cell >= s->N) return HYDRO_ERR_INVALID_ARG;
+    AuxArgs a = aux_args(s, s->buf[s->cur]);
+    s->launches += 1;
+    cudaError_t e = launch_poke(a, var, cell, v, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
+}
+
+int hydro_set_zchunk(hydro_sim *s, int zchunk)
+{
+    if (!s || zchunk < 0) return HYDRO_ERR_INVALID_ARG;
+    if (s->prob.ndim == 2) return zchunk <= 1 ? HYDRO_OK : HYDRO_ERR_INVALID_ARG;
+    s->zchunk = zchunk == 0 ? default_zchunk(s) : std::min(zchunk, s->prob.n[2]);
+    return HYDRO_OK;
+}
+
+long hydro_launch_count(hydro_sim *s) { return s ? s->launches : -1; }
+
+int hydro_destroy(hydro_sim *s)
+{
+    if (!s) return HYDRO_ERR_INVALID_ARG;
+    cudaStreamSynchronize(s->stream);
+    delete s;
+    return HYDRO_OK;
+}
+
+const char *hydro_strerror(int status)
+{
+    switch (status) {
+    case HYDRO_OK: return "ok";
+    case HYDRO_ERR_INVALID_ARG: return "invalid argument";
+    case HYDRO_ERR_OOM: return "buffer too small";
+    case HYDRO_ERR_CUDA: return "CUDA error";
+    case HYDRO_ERR_NONPHYSICAL: return "non-physical state (density or pressure not positive or not finite)";
+    case HYDRO_ERR_TIMEOUT: return "bounded device wait timed out";
+    case HYDRO_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// hydro_internal.h -- structures shared by the host API and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace hydro {
+
+enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2 };
+
+// Device-resident time control; one per handle, at the start of the
+// workspace.  Written only by the last CTA of a step (or of the dt kernel),
+// read by every CTA of the next launch on the same stream.
+struct __align__(16) Ctrl {
+    double t;           // current time
+    double dt_next;     // cfl / max signal speed of the current state
+    double dt_last;     // dt taken by the last step
+    double max_speed;   // max signal speed of the current state
+    long long step;     // steps since init / set_state
+    unsigned int counter;   // last-CTA arrival counter (returns to 0)
+    int err;            // committed error bits (changed only at finalisation)
+    int err_new;        // error bits raised by CTAs of the running step
+    int pad0;
+    double totals[5];   // last conserved-total reduction
+    double pad[2];
+};
+
+// Per z-plane background constants of the hydrostatic-background mode, FP64,
+// for planes k = -2 .. nz+2 (entry k + 2).
+struct PlaneBG {
+    double rho_c, p_c;  // background at the plane centre (0 for k = nz+2)
+    double rho_f, p_f;  // background at the plane's low face z_lo + k dz
+    double drho, dp;    // face(k+1) - face(k) (0 for k = nz+2)
+    double B;           // (p_f(k+1) - p_f(k))/dz - rho_c g_z: discrete imbalance
+    double pad;
+};
+
+// Arguments of one step launch (passed by value).
+struct StepArgs {
+    const void *U;      // state at t^n
+    void *Unew;         // state at t^{n+1}
+    int n[3];
+    long long plane;    // nx*ny
+    long long vstride;  // nx*ny*nz: distance between variable planes
+    int bc_lo[3], bc_hi[3];
+    double inv_dx[3];
+    double gamma, cfl;
+    double grav[3];
+    double t_end;       // clamp target (+inf for a free step)
+    Ctrl *ctrl;
+    double *partial;    // per-CTA max signal speed
+    const PlaneBG *bg;  // hse tables (nullptr in plain mode)
+    int zchunk;         // planes per CTA (3D)
+    int tiles_x;        // tiles along x
+};
+
+// Workspace layout (offsets in bytes from the workspace base).
+struct WorkLayout {
+    size_t ctrl, partial, bg, red, total;
+    int max_ctas;
+};
+
+}  // namespace hydro

@@ -1,0 +1,53 @@
+// launchers.h -- host-side launch entry points of the kernels (one
+// translation unit per precision family so they compile in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hydro_internal.h"
+
+namespace hydro {
+
+// 3D step tile: TX x TY threads, one column of cells each.
+constexpr int STEP3D_TX = 32;
+constexpr int STEP3D_TY = 8;
+// 2D step tile.
+constexpr int STEP2D_TX = 32;
+constexpr int STEP2D_TY = 8;
+
+cudaError_t launch_step3d_f64(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
+cudaError_t launch_step3d_f32(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
+cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32);
+
+// Auxiliary kernels (aux.cu).  fp32 selects the stored precision.
+struct AuxArgs {
+    void *U;              // stored state
+    int ndim, n[3];
+    long long N, plane;
+    double gamma, cfl, inv_dx[3], cell_volume;
+    Ctrl *ctrl;
+    double *partial;      // per-CTA partials (max_ctas * 5 doubles)
+    const PlaneBG *bg;    // hse tables or nullptr
+    int hse, fp32;
+};
+
+// staging (FP64 primitives of cells [c0, c0 + m), planes of length m) -> state
+cudaError_t launch_init_convert(const AuxArgs &a, const double *staging, long long c0,
+                                long long m, cudaStream_t s);
+// max signal speed of the state -> ctrl->dt_next (time unchanged)
+cudaError_t launch_signal(const AuxArgs &a, cudaStream_t s);
+// FP64 conserved totals (fixed-order two-stage sum) -> ctrl->totals
+cudaError_t launch_totals(const AuxArgs &a, cudaStream_t s);
+// state cells [c0, c0 + m) -> FP64 total conserved (what = 0) or primitive
+// (what = 1) variables in staging (planes of length m)
+cudaError_t launch_fields(const AuxArgs &a, double *staging, long long c0, long long m,
+                          int what, cudaStream_t s);
+// one stored value
+cudaError_t launch_poke(const AuxArgs &a, int var, long long cell, double v, cudaStream_t s);
+
+// grid of the reduction kernels (a fixed function of N, so sums are
+// bitwise reproducible)
+int aux_reduce_blocks(long long N);
+constexpr int AUX_THREADS = 256;
+
+}  // namespace hydro

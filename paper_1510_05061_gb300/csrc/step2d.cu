@@ -1,0 +1,28 @@
+// step2d.cu -- FP64 and FP32 instantiations of the fused 2D step.
+#include "launchers.h"
+#include "step2d.cuh"
+
+namespace hydro {
+
+template <typename T>
+static cudaError_t launch2d(const StepArgs &a, dim3 grid, cudaStream_t s)
+{
+    constexpr int TX = STEP2D_TX, TY = STEP2D_TY;
+    auto k = step2d_kernel<T, TX, TY>;
+    constexpr size_t smem = Step2DSmem<T, TX, TY>::bytes;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<grid, TX * TY, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32)
+{
+    return fp32 ? launch2d<float>(a, grid, s) : launch2d<double>(a, grid, s);
+}
+
+}  // namespace hydro

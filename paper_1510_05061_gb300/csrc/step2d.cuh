@@ -1,0 +1,217 @@
+// step2d.cuh -- one unsplit finite-volume step of the 2D compressible Euler
+// equations, fused into a single kernel.
+//
+// A CTA owns a TX x TY tile.  It stages the tile plus a depth-2 halo of U^n
+// in shared memory (boundary conditions by index mapping) as primitives,
+// computes the MC slopes and MUSCL-Hancock half step of the tile and of the
+// one-cell cross-shaped ring whose faces border the tile, evaluates every
+// x and y face flux of the tile once (HLLC), then applies the flux
+// divergence and gravity sources, stores U^{n+1}, checks admissibility and
+// reduces the CFL signal speed (last-CTA FP64 dt on the device).
+#pragma once
+
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+template <typename T, int TX, int TY>
+struct Step2DSmem {
+    static constexpr int NV = 4;
+    static constexpr int HX = TX + 4, HY = TY + 4;
+    static constexpr size_t prim = (size_t)NV * HY * HX;
+    static constexpr size_t wx = (size_t)NV * TY * (TX + 2);
+    static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;
+    static constexpr size_t fx = (size_t)NV * TY * (TX + 1);
+    static constexpr size_t fy = (size_t)NV * (TY + 1) * TX;
+    static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy;
+    static constexpr size_t bytes = elems * sizeof(T);
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
+{
+    constexpr int ND = 2, NV = 4, NT = TX * TY;
+    using S = Step2DSmem<T, TX, TY>;
+    constexpr int HX = S::HX, HY = S::HY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *prim = reinterpret_cast<T *>(smem_raw);
+    T *wxl = prim + S::prim, *wxh = wxl + S::wx;
+    T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
+    T *fxs = wyh + S::wy, *fys = fxs + S::fx;
+    __shared__ double red[32];
+    __shared__ int s_last;
+
+    const int nx = a.n[0], ny = a.n[1];
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int x0 = (blockIdx.x % a.tiles_x) * TX;
+    const int y0 = (blockIdx.x / a.tiles_x) * TY;
+    const int nblocks = gridDim.x * gridDim.y;
+    const T *__restrict__ U = static_cast<const T *>(a.U);
+    T *__restrict__ Un = static_cast<T *>(a.Unew);
+    const long long vs = a.vstride;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < nx && gy < ny;
+
+    const double t_now = a.ctrl->t;
+    const double dt_cfl = a.ctrl->dt_next;
+    if (t_now >= a.t_end || a.ctrl->err != 0) {
+        if (own)
+            for (int q = 0; q < NV; ++q) {
+                const size_t c = (size_t)q * vs + (size_t)gy * nx + gx;
+                Un[c] = U[c];
+            }
+        return;
+    }
+    const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
+    const T dt = T(dtd), hdt = T(0.5) * T(dtd);
+    const T gam = T(a.gamma);
+    const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(0)};
+    const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(0)};
+
+    auto P = [&](int q, int hy, int hx) -> T & { return prim[((size_t)q * HY + hy) * HX + hx]; };
+    auto WX = [&](T *base, int q, int cy, int cx) -> T & {
+        return base[((size_t)q * TY + cy) * (TX + 2) + cx + 1];
+    };
+    auto WY = [&](T *base, int q, int cy, int cx) -> T & {
+        return base[((size_t)q * (TY + 2) + cy + 1) * TX + cx];
+    };
+    auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[((size_t)q * TY + cy) * (TX + 1) + fxi]; };
+    auto FY = [&](int q, int fyi, int cx) -> T & { return fys[((size_t)q * (TY + 1) + fyi) * TX + cx]; };
+
+    // ---- stage the haloed tile as primitives
+    for (int i = tid; i < HX * HY; i += NT) {
+        const int hx = i % HX, hy = i / HX;
+        bool fx, fy;
+        const int sx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
+        const int sy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
+        const size_t c = (size_t)sy * nx + sx;
+        const T r = U[c];
+        T m0 = U[c + vs], m1 = U[c + 2 * vs];
+        const T e = U[c + 3 * vs];
+        if (fx) m0 = -m0;
+        if (fy) m1 = -m1;
+        const T rinv = T(1) / r;
+        P(0, hy, hx) = r;
+        P(1, hy, hx) = m0 * rinv;
+        P(2, hy, hx) = m1 * rinv;
+        P(3, hy, hx) = (gam - T(1)) * (e - T(0.5) * (m0 * m0 + m1 * m1) * rinv);
+    }
+    __syncthreads();
+
+    const CellBG<T> nobg = cell_bg<T, false>(nullptr, 0);
+    auto predict = [&](int cx, int cy, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
+        const int hx = cx + 2, hy = cy + 2;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const T c = P(q, hy, hx);
+            w[q] = c;
+            dw[0][q] = mc_slope(c - P(q, hy, hx - 1), P(q, hy, hx + 1) - c);
+            dw[1][q] = mc_slope(c - P(q, hy - 1, hx), P(q, hy + 1, hx) - c);
+        }
+        hancock<T, ND, false>(w, dw, wh, hdt, inv_dx, gam, grav, nobg);
+    };
+
+    // ---- half step: tile cells, then the cross-shaped ring
+    {
+        T w[NV], dw[ND][NV], wh[NV];
+        predict(tx, ty, w, dw, wh);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            WX(wxl, q, ty, tx) = wh[q] - T(0.5) * dw[0][q];
+            WX(wxh, q, ty, tx) = wh[q] + T(0.5) * dw[0][q];
+            WY(wyl, q, ty, tx) = wh[q] - T(0.5) * dw[1][q];
+            WY(wyh, q, ty, tx) = wh[q] + T(0.5) * dw[1][q];
+        }
+    }
+    constexpr int NRING = 2 * TY + 2 * TX;
+    for (int i = tid; i < NRING; i += NT) {
+        int cx, cy;
+        bool xside;
+        if (i < 2 * TY) { xside = true; cy = i >> 1; cx = (i & 1) ? TX : -1; }
+        else { xside = false; const int j = i - 2 * TY; cx = j >> 1; cy = (j & 1) ? TY : -1; }
+        T w[NV], dw[ND][NV], wh[NV];
+        predict(cx, cy, w, dw, wh);
+        if (xside) {
+            if (cx < 0) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) WX(wxh, q, cy, cx) = wh[q] + T(0.5) * dw[0][q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) WX(wxl, q, cy, cx) = wh[q] - T(0.5) * dw[0][q];
+            }
+        } else {
+            if (cy < 0) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) WY(wyh, q, cy, cx) = wh[q] + T(0.5) * dw[1][q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) WY(wyl, q, cy, cx) = wh[q] - T(0.5) * dw[1][q];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- face fluxes
+    for (int i = tid; i < (TX + 1) * TY; i += NT) {
+        const int fi = i % (TX + 1), cy = i / (TX + 1);
+        T wl[NV], wr[NV], f[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { wl[q] = WX(wxh, q, cy, fi - 1); wr[q] = WX(wxl, q, cy, fi); }
+        const int gf = x0 + fi;
+        if (gf == 0 && a.bc_lo[0] == BC_REFLECT) mirror_state<T, NV, 0>(wr, wl);
+        if (gf == nx && a.bc_hi[0] == BC_REFLECT) mirror_state<T, NV, 0>(wl, wr);
+        hllc<T, ND, 0, false>(wl, wr, T(0), T(0), gam, f);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
+    }
+    for (int i = tid; i < TX * (TY + 1); i += NT) {
+        const int cx = i % TX, fi = i / TX;
+        T wl[NV], wr[NV], f[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { wl[q] = WY(wyh, q, fi - 1, cx); wr[q] = WY(wyl, q, fi, cx); }
+        const int gf = y0 + fi;
+        if (gf == 0 && a.bc_lo[1] == BC_REFLECT) mirror_state<T, NV, 1>(wr, wl);
+        if (gf == ny && a.bc_hi[1] == BC_REFLECT) mirror_state<T, NV, 1>(wl, wr);
+        hllc<T, ND, 1, false>(wl, wr, T(0), T(0), gam, f);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
+    }
+    __syncthreads();
+
+    // ---- update, admissibility, CFL signal speed
+    double smax = 0.0;
+    bool bad = false;
+    if (own) {
+        const size_t c = (size_t)gy * nx + gx;
+        T u[NV], du[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            u[q] = U[c + q * vs];
+            du[q] = -((FX(q, ty, tx + 1) - FX(q, ty, tx)) * inv_dx[0]
+                      + (FY(q, ty + 1, tx) - FY(q, ty, tx)) * inv_dx[1]);
+        }
+        const T msrc = grav[0] * T(0.5) * (FX(0, ty, tx) + FX(0, ty, tx + 1))
+                     + grav[1] * T(0.5) * (FY(0, ty, tx) + FY(0, ty + 1, tx));
+        const T r_old = u[0];
+        const T r_new = r_old + dt * du[0];
+        u[0] = r_new;
+        const T rsum = T(0.5) * (r_old + r_new);
+        u[1] += dt * (du[1] + grav[0] * rsum);
+        u[2] += dt * (du[2] + grav[1] * rsum);
+        u[3] += dt * (du[3] + msrc);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
+        const T rinv = T(1) / u[0];
+        const T vx = u[1] * rinv, vy = u[2] * rinv;
+        const T pres = (gam - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
+        const T cs = sqrt(gam * pres * rinv);
+        const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1];
+        if (!(u[0] > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
+        else smax = double(s);
+    }
+    const bool bad_cta = __syncthreads_or(bad) != 0;
+    const double m = block_max<NT>(smax, red);
+    finish_step<NT>(m, bad_cta, a, nblocks, dtd, true, &s_last);
+}
+
+}  // namespace hydro

@@ -1,0 +1,319 @@
+// step3d.cuh -- one unsplit finite-volume step of the 3D compressible Euler
+// equations, fused into a single kernel.
+//
+// Decomposition (2.5-D blocking): a CTA owns a TX x TY column of cells in the
+// x-y plane and marches up a chunk of z planes [z0, z1).  Per plane p it
+//   1. stages plane p+1 of U^n with a depth-2 x-y halo in shared memory,
+//      boundary conditions applied by index mapping, converted to
+//      primitives (a 3-plane ring: p-1, p, p+1);
+//   2. computes MC slopes and the MUSCL-Hancock half step of plane p for the
+//      cells that own a needed face: the tile plus a one-cell cross-shaped
+//      ring; x/y face states go to shared memory, the z face states of the
+//      thread's own column stay in registers;
+//   3. evaluates each x and y face flux of plane p once (HLLC) and the z
+//      flux at p - 1/2 (thread's own column);
+//   4. completes plane p-1: flux divergence, gravity sources, store of
+//      U^{n+1}, positivity check and the cell's CFL signal speed.
+// The only HBM traffic is one read of U^n (plus halo re-reads, mostly L2
+// hits) and one write of U^{n+1}.  The CTA max signal speed feeds a
+// last-CTA FP64 reduction that sets the next dt on the device.
+#pragma once
+
+#include "hydro_device.cuh"
+
+namespace hydro {
+
+template <typename T, bool HSE, int TX, int TY>
+struct Step3DSmem {
+    static constexpr int NV = 5;
+    static constexpr int HX = TX + 4, HY = TY + 4;
+    static constexpr size_t prim = 3ull * NV * HY * HX;        // [3][NV][HY][HX]
+    static constexpr size_t wx = (size_t)NV * TY * (TX + 2);   // [NV][TY][TX+2]
+    static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;   // [NV][TY+2][TX]
+    static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
+    static constexpr size_t fy = (size_t)NV * (TY + 1) * TX;   // [NV][TY+1][TX]
+    static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy;
+    static constexpr size_t bytes = elems * sizeof(T);
+};
+
+template <typename T, bool HSE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
+{
+    constexpr int ND = 3, NV = 5, NT = TX * TY;
+    using S = Step3DSmem<T, HSE, TX, TY>;
+    constexpr int HX = S::HX, HY = S::HY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *prim = reinterpret_cast<T *>(smem_raw);
+    T *wxl = prim + S::prim, *wxh = wxl + S::wx;
+    T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
+    T *fxs = wyh + S::wy, *fys = fxs + S::fx;
+    __shared__ double red[32];
+    __shared__ int s_last;
+
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int x0 = (blockIdx.x % a.tiles_x) * TX;
+    const int y0 = (blockIdx.x / a.tiles_x) * TY;
+    const int z0 = blockIdx.y * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, nz);
+    const int nblocks = gridDim.x * gridDim.y;
+    const T *__restrict__ U = static_cast<const T *>(a.U);
+    T *__restrict__ Un = static_cast<T *>(a.Unew);
+    const long long vs = a.vstride;
+
+    // ---- time control: dt from the device block, clamped to t_end
+    const double t_now = a.ctrl->t;
+    const double dt_cfl = a.ctrl->dt_next;
+    if (t_now >= a.t_end || a.ctrl->err != 0) {
+        // finished or failed: carry the state over unchanged
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx < nx && gy < ny)
+            for (int k = z0; k < z1; ++k)
+                for (int q = 0; q < NV; ++q) {
+                    const size_t c = (size_t)q * vs + (size_t)k * a.plane + (size_t)gy * nx + gx;
+                    Un[c] = U[c];
+                }
+        return;
+    }
+    const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
+    const T dt = T(dtd), hdt = T(0.5) * T(dtd);
+    const T gam = T(a.gamma);
+    const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(a.inv_dx[2])};
+    const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(a.grav[2])};
+
+    auto P = [&](int slot, int q, int hy, int hx) -> T & {
+        return prim[((size_t)(slot * NV + q) * HY + hy) * HX + hx];
+    };
+
+    // ---- stage plane pz (may be a ghost plane) into ring slot
+    auto load_plane = [&](int pz) {
+        const int slot = (pz + 3) % 3;
+        bool fz;
+        const int gz = map_index(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
+        const T rho_bg = HSE ? T(a.bg[pz + 2].rho_c) : T(0);
+        for (int i = tid; i < HX * HY; i += NT) {
+            const int hx = i % HX, hy = i / HX;
+            bool fx, fy;
+            const int gx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
+            const int gy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
+            const size_t c = (size_t)gz * a.plane + (size_t)gy * nx + gx;
+            const T r = U[c];
+            T m0 = U[c + vs], m1 = U[c + 2 * vs], m2 = U[c + 3 * vs];
+            const T e = U[c + 4 * vs];
+            if (fx) m0 = -m0;
+            if (fy) m1 = -m1;
+            if (fz) m2 = -m2;
+            const T rho = HSE ? rho_bg + r : r;
+            const T rinv = T(1) / rho;
+            P(slot, 0, hy, hx) = r;
+            P(slot, 1, hy, hx) = m0 * rinv;
+            P(slot, 2, hy, hx) = m1 * rinv;
+            P(slot, 3, hy, hx) = m2 * rinv;
+            P(slot, 4, hy, hx) = (gam - T(1)) * (e - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+        }
+    };
+
+    // ---- slopes + half step of the cell at local (cx, cy) of plane p
+    auto predict = [&](int cx, int cy, int p, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
+        const int s0 = (p + 3) % 3, sm = (p + 2) % 3, sp = (p + 4) % 3;
+        const int hx = cx + 2, hy = cy + 2;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const T c = P(s0, q, hy, hx);
+            w[q] = c;
+            dw[0][q] = mc_slope(c - P(s0, q, hy, hx - 1), P(s0, q, hy, hx + 1) - c);
+            dw[1][q] = mc_slope(c - P(s0, q, hy - 1, hx), P(s0, q, hy + 1, hx) - c);
+            dw[2][q] = mc_slope(c - P(sm, q, hy, hx), P(sp, q, hy, hx) - c);
+        }
+        const CellBG<T> bg = cell_bg<T, HSE>(a.bg, p);
+        hancock<T, ND, HSE>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
+    };
+
+    auto WX = [&](T *base, int q, int cy, int cx) -> T & {   // cx in [-1, TX]
+        return base[((size_t)q * TY + cy) * (TX + 2) + cx + 1];
+    };
+    auto WY = [&](T *base, int q, int cy, int cx) -> T & {   // cy in [-1, TY]
+        return base[((size_t)q * (TY + 2) + cy + 1) * TX + cx];
+    };
+    auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[((size_t)q * TY + cy) * (TX + 1) + fxi]; };
+    auto FY = [&](int q, int fyi, int cx) -> T & { return fys[((size_t)q * (TY + 1) + fyi) * TX + cx]; };
+
+    // register pipeline of the thread's own column
+    T ztop_prev[NV], fz_prev[NV], div_prev[NV];
+    T msrc_prev = T(0);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { ztop_prev[q] = T(0); fz_prev[q] = T(0); div_prev[q] = T(0); }
+    double smax = 0.0;
+    bool bad = false;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < nx && gy < ny;
+
+    load_plane(z0 - 2);
+    load_plane(z0 - 1);
+    for (int p = z0 - 1; p <= z1; ++p) {
+        load_plane(p + 1);
+        __syncthreads();
+        const bool xy = (p >= z0 && p < z1);
+
+        // ---- step 2: half step; own cell first (z faces kept in registers)
+        T zlo[NV], ztop[NV];
+        {
+            T w[NV], dw[ND][NV], wh[NV];
+            predict(tx, ty, p, w, dw, wh);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                zlo[q] = wh[q] - T(0.5) * dw[2][q];
+                ztop[q] = wh[q] + T(0.5) * dw[2][q];
+            }
+            if (xy) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    WX(wxl, q, ty, tx) = wh[q] - T(0.5) * dw[0][q];
+                    WX(wxh, q, ty, tx) = wh[q] + T(0.5) * dw[0][q];
+                    WY(wyl, q, ty, tx) = wh[q] - T(0.5) * dw[1][q];
+                    WY(wyh, q, ty, tx) = wh[q] + T(0.5) * dw[1][q];
+                }
+            }
+        }
+        if (xy) {
+            // ring cells: x = -1 and x = TX (rows 0..TY-1), y = -1 and y = TY
+            // (columns 0..TX-1); only their face toward the tile is needed
+            constexpr int NRING = 2 * TY + 2 * TX;
+            for (int i = tid; i < NRING; i += NT) {
+                int cx, cy;
+                bool xside;
+                if (i < 2 * TY) { xside = true; cy = i >> 1; cx = (i & 1) ? TX : -1; }
+                else { xside = false; const int j = i - 2 * TY; cx = j >> 1; cy = (j & 1) ? TY : -1; }
+                T w[NV], dw[ND][NV], wh[NV];
+                predict(cx, cy, p, w, dw, wh);
+                if (xside) {
+                    if (cx < 0) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) WX(wxh, q, cy, cx) = wh[q] + T(0.5) * dw[0][q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) WX(wxl, q, cy, cx) = wh[q] - T(0.5) * dw[0][q];
+                    }
+                } else {
+                    if (cy < 0) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) WY(wyh, q, cy, cx) = wh[q] + T(0.5) * dw[1][q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) WY(wyl, q, cy, cx) = wh[q] - T(0.5) * dw[1][q];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- step 3: face fluxes
+        const T rb_c = HSE ? T(a.bg[p + 2].rho_c) : T(0);
+        const T pb_c = HSE ? T(a.bg[p + 2].p_c) : T(0);
+        if (xy) {
+            for (int i = tid; i < (TX + 1) * TY; i += NT) {
+                const int fi = i % (TX + 1), cy = i / (TX + 1);
+                T wl[NV], wr[NV], f[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) { wl[q] = WX(wxh, q, cy, fi - 1); wr[q] = WX(wxl, q, cy, fi); }
+                const int gf = x0 + fi;
+                if (gf == 0 && a.bc_lo[0] == BC_REFLECT) mirror_state<T, NV, 0>(wr, wl);
+                if (gf == nx && a.bc_hi[0] == BC_REFLECT) mirror_state<T, NV, 0>(wl, wr);
+                hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, f);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
+            }
+            for (int i = tid; i < TX * (TY + 1); i += NT) {
+                const int cx = i % TX, fi = i / TX;
+                T wl[NV], wr[NV], f[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) { wl[q] = WY(wyh, q, fi - 1, cx); wr[q] = WY(wyl, q, fi, cx); }
+                const int gf = y0 + fi;
+                if (gf == 0 && a.bc_lo[1] == BC_REFLECT) mirror_state<T, NV, 1>(wr, wl);
+                if (gf == ny && a.bc_hi[1] == BC_REFLECT) mirror_state<T, NV, 1>(wl, wr);
+                hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, f);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
+            }
+        }
+        T fz[NV];
+        if (p >= z0) {
+            // z face p - 1/2 between the top of cell p-1 and the bottom of cell p
+            T wl[NV], wr[NV];
+            if (p == 0 && a.bc_lo[2] == BC_REFLECT) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) wr[q] = zlo[q];
+                mirror_state<T, NV, 2>(wr, wl);
+            } else if (p == nz && a.bc_hi[2] == BC_REFLECT) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) wl[q] = ztop_prev[q];
+                mirror_state<T, NV, 2>(wl, wr);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) { wl[q] = ztop_prev[q]; wr[q] = zlo[q]; }
+            }
+            const T rb_f = HSE ? T(a.bg[p + 2].rho_f) : T(0);
+            const T pb_f = HSE ? T(a.bg[p + 2].p_f) : T(0);
+            hllc<T, ND, 2, HSE>(wl, wr, rb_f, pb_f, gam, fz);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) fz[q] = T(0);
+        }
+        __syncthreads();
+
+        // ---- step 4: complete plane p-1 (an output plane when p > z0)
+        if (p > z0 && own) {
+            const int k = p - 1;
+            const size_t c = (size_t)k * a.plane + (size_t)gy * nx + gx;
+            T u[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = U[c + q * vs];
+            T du[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) du[q] = -(div_prev[q] + (fz[q] - fz_prev[q]) * inv_dx[2]);
+            const T msrc = msrc_prev + grav[2] * T(0.5) * (fz_prev[0] + fz[0]);
+            const T r_old = u[0];
+            const T r_new = r_old + dt * du[0];
+            u[0] = r_new;
+            const T rsum = T(0.5) * (r_old + r_new);
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                T src = grav[d] * rsum;
+                if (HSE && d == 2) src -= T(a.bg[k + 2].B);
+                u[1 + d] += dt * (du[1 + d] + src);
+            }
+            u[4] += dt * (du[4] + msrc);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
+            // CFL signal speed and admissibility of the new state
+            const T rho = HSE ? T(a.bg[k + 2].rho_c) + u[0] : u[0];
+            const T rinv = T(1) / rho;
+            const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
+            const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
+            const T pres = HSE ? T(a.bg[k + 2].p_c) + pp : pp;
+            const T cs = sqrt(gam * pres * rinv);
+            const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
+            if (!(rho > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
+            else smax = fmax(smax, double(s));
+        }
+        if (xy) {
+            T dv[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+                dv[q] = (FX(q, ty, tx + 1) - FX(q, ty, tx)) * inv_dx[0]
+                      + (FY(q, ty + 1, tx) - FY(q, ty, tx)) * inv_dx[1];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) div_prev[q] = dv[q];
+            msrc_prev = grav[0] * T(0.5) * (FX(0, ty, tx) + FX(0, ty, tx + 1))
+                      + grav[1] * T(0.5) * (FY(0, ty, tx) + FY(0, ty + 1, tx));
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { ztop_prev[q] = ztop[q]; fz_prev[q] = fz[q]; }
+    }
+
+    const bool bad_cta = __syncthreads_or(bad) != 0;
+    const double m = block_max<NT>(smax, red);
+    finish_step<NT>(m, bad_cta, a, nblocks, dtd, true, &s_last);
+}
+
+}  // namespace hydro

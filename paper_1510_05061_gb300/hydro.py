@@ -1,0 +1,344 @@
+"""Python binding of libhydro (include/hydro.h): argument marshalling only.
+
+Module-level functions carry the C names (hydro_init, hydro_step,
+hydro_advance_to, hydro_reduce, ...) and map one to one onto the C ABI; every
+step of the update runs in the library's CUDA kernels.  ``Simulation`` wraps a
+handle with PyTorch-owned device buffers on the current CUDA stream.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1510_05061_gb300.build``); loading fails loudly otherwise.
+There is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhydro.so")
+
+HYDRO_OK = 0
+HYDRO_ERR_INVALID_ARG = -1
+HYDRO_ERR_OOM = -2
+HYDRO_ERR_CUDA = -3
+HYDRO_ERR_NONPHYSICAL = -4
+HYDRO_ERR_TIMEOUT = -5
+HYDRO_ERR_STATE = -6
+
+HYDRO_RED_TOTALS = 1
+HYDRO_RED_DT = 2
+HYDRO_RED_TIME = 3
+HYDRO_RED_MAXSPEED = 4
+HYDRO_RED_STEP = 5
+HYDRO_RED_DT_LAST = 6
+
+# every symbol include/hydro.h declares
+EXPORTS = (
+    "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_step",
+    "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
+    "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk",
+    "hydro_launch_count", "hydro_destroy", "hydro_strerror",
+)
+
+
+class hydro_problem(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int), ("n", C.c_int * 3),
+        ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3),
+        ("gamma", C.c_double), ("cfl", C.c_double), ("grav", C.c_double * 3),
+        ("precision", C.c_int), ("hse_subtract", C.c_int),
+    ]
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = _lib.hydro_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhydro.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libhydro.so not built at {path}; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    P = C.POINTER(hydro_problem)
+    vp, D = C.c_void_p, C.POINTER(C.c_double)
+    L.hydro_state_bytes.restype = C.c_size_t
+    L.hydro_state_bytes.argtypes = [P]
+    L.hydro_workspace_bytes.restype = C.c_size_t
+    L.hydro_workspace_bytes.argtypes = [P]
+    L.hydro_init.restype = C.c_int
+    L.hydro_init.argtypes = [P, vp, vp, vp, D, D, vp, C.POINTER(vp)]
+    L.hydro_step.restype = C.c_int
+    L.hydro_step.argtypes = [vp, D]
+    L.hydro_advance_to.restype = C.c_int
+    L.hydro_advance_to.argtypes = [vp, C.c_double, C.c_long, C.POINTER(C.c_long), D]
+    L.hydro_reduce.restype = C.c_int
+    L.hydro_reduce.argtypes = [vp, C.c_int, D]
+    L.hydro_current.restype = vp
+    L.hydro_current.argtypes = [vp]
+    L.hydro_get_state.restype = C.c_int
+    L.hydro_get_state.argtypes = [vp, vp]
+    L.hydro_set_state.restype = C.c_int
+    L.hydro_set_state.argtypes = [vp, vp, C.c_double, C.c_long]
+    L.hydro_get_fields.restype = C.c_int
+    L.hydro_get_fields.argtypes = [vp, C.c_int, D]
+    L.hydro_debug_poke.restype = C.c_int
+    L.hydro_debug_poke.argtypes = [vp, C.c_int, C.c_long, C.c_double]
+    L.hydro_set_zchunk.restype = C.c_int
+    L.hydro_set_zchunk.argtypes = [vp, C.c_int]
+    L.hydro_launch_count.restype = C.c_long
+    L.hydro_launch_count.argtypes = [vp]
+    L.hydro_destroy.restype = C.c_int
+    L.hydro_destroy.argtypes = [vp]
+    L.hydro_strerror.restype = C.c_char_p
+    L.hydro_strerror.argtypes = [C.c_int]
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != HYDRO_OK:
+        raise HydroError(rc, what)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_problem(p: "inputs.Problem") -> hydro_problem:
+    s = hydro_problem()
+    s.ndim = p.ndim
+    for d in range(3):
+        s.n[d] = int(p.n[d])
+        s.lo[d] = float(p.lo[d])
+        s.hi[d] = float(p.hi[d])
+        s.bc_lo[d] = int(p.bc_lo[d])
+        s.bc_hi[d] = int(p.bc_hi[d])
+        s.grav[d] = float(p.grav[d])
+    s.gamma = float(p.gamma)
+    s.cfl = float(p.cfl)
+    s.precision = int(p.precision)
+    s.hse_subtract = int(p.hse_subtract)
+    return s
+
+
+def background_tables(p: "inputs.Problem") -> Optional[np.ndarray]:
+    """The hse tables in the order hydro_init expects, or None."""
+    if not p.hse_subtract:
+        return None
+    nz = p.n[2]
+    parts = [np.asarray(p.bg_rho_c, np.float64), np.asarray(p.bg_p_c, np.float64),
+             np.asarray(p.bg_rho_f, np.float64), np.asarray(p.bg_p_f, np.float64)]
+    want = (nz + 4, nz + 4, nz + 5, nz + 5)
+    if tuple(x.size for x in parts) != want:
+        raise ValueError(f"background tables must have lengths {want}")
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+# ----------------------------------------------------------- C-named calls
+
+def hydro_state_bytes(prob: hydro_problem) -> int:
+    return load().hydro_state_bytes(C.byref(prob))
+
+
+def hydro_workspace_bytes(prob: hydro_problem) -> int:
+    return load().hydro_workspace_bytes(C.byref(prob))
+
+
+def hydro_init(prob: hydro_problem, Ua: int, Ub: int, work: int, W0: np.ndarray,
+               bg: Optional[np.ndarray], stream: int) -> C.c_void_p:
+    h = C.c_void_p()
+    rc = load().hydro_init(C.byref(prob), C.c_void_p(Ua), C.c_void_p(Ub), C.c_void_p(work),
+                           _dptr(W0), _dptr(bg), C.c_void_p(stream), C.byref(h))
+    if rc != HYDRO_OK and h.value:
+        load().hydro_destroy(h)
+    _check(rc, "hydro_init")
+    return h
+
+
+def hydro_step(h, want_dt: bool = False) -> Optional[float]:
+    dt = C.c_double(0.0)
+    _check(load().hydro_step(h, C.byref(dt) if want_dt else None), "hydro_step")
+    return dt.value if want_dt else None
+
+
+def hydro_advance_to(h, t_end: float, max_steps: int = 1 << 40):
+    n, t = C.c_long(0), C.c_double(0.0)
+    _check(load().hydro_advance_to(h, float(t_end), int(max_steps), C.byref(n), C.byref(t)),
+           "hydro_advance_to")
+    return n.value, t.value
+
+
+def hydro_reduce(h, what: int, nvar: int = 1) -> np.ndarray:
+    out = np.zeros(max(nvar, 1), dtype=np.float64)
+    _check(load().hydro_reduce(h, int(what), _dptr(out)), "hydro_reduce")
+    return out
+
+
+def hydro_current(h) -> int:
+    return load().hydro_current(h)
+
+
+def hydro_get_state(h, dst: np.ndarray):
+    _check(load().hydro_get_state(h, C.c_void_p(dst.ctypes.data)), "hydro_get_state")
+
+
+def hydro_set_state(h, src: np.ndarray, t: float, step: int):
+    _check(load().hydro_set_state(h, C.c_void_p(src.ctypes.data), float(t), int(step)),
+           "hydro_set_state")
+
+
+def hydro_get_fields(h, what: int, dst: np.ndarray):
+    _check(load().hydro_get_fields(h, int(what), _dptr(dst)), "hydro_get_fields")
+
+
+def hydro_debug_poke(h, var: int, cell: int, v: float):
+    _check(load().hydro_debug_poke(h, int(var), int(cell), float(v)), "hydro_debug_poke")
+
+
+def hydro_set_zchunk(h, z: int):
+    _check(load().hydro_set_zchunk(h, int(z)), "hydro_set_zchunk")
+
+
+def hydro_launch_count(h) -> int:
+    return load().hydro_launch_count(h)
+
+
+def hydro_destroy(h):
+    _check(load().hydro_destroy(h), "hydro_destroy")
+
+
+# --------------------------------------------------------------- wrapper
+
+class Simulation:
+    """One solve: torch-owned device buffers bound to a libhydro handle.
+
+    W0 is the host FP64 array of total primitive fields (rho, u.., p) of
+    shape prob.shape.  Runs on ``stream`` (a torch.cuda.Stream) or on the
+    current stream of the current device.
+    """
+
+    def __init__(self, prob: "inputs.Problem", W0: np.ndarray, stream=None, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhydro needs a CUDA device")
+        self.prob = prob
+        self.cp = make_problem(prob)
+        sb = hydro_state_bytes(self.cp)
+        wb = hydro_workspace_bytes(self.cp)
+        if sb == 0 or wb == 0:
+            raise HydroError(HYDRO_ERR_INVALID_ARG, "problem")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        # 256-byte aligned device buffers owned by torch
+        self._bufs = [torch.empty(n + 256, dtype=torch.uint8, device=dev) for n in (sb, sb, wb)]
+        ptrs = [(b.data_ptr() + 255) // 256 * 256 for b in self._bufs]
+        self.state_bytes, self.work_bytes = sb, wb
+        self._W0 = np.ascontiguousarray(W0, dtype=np.float64)
+        if self._W0.shape != tuple(prob.shape):
+            raise ValueError(f"W0 shape {self._W0.shape} != {prob.shape}")
+        self._bg = background_tables(prob)
+        with torch.cuda.device(dev):
+            self.h = hydro_init(self.cp, ptrs[0], ptrs[1], ptrs[2], self._W0, self._bg,
+                                self.stream.cuda_stream)
+
+    # stepping ---------------------------------------------------------
+    def step(self, want_dt: bool = False):
+        return hydro_step(self.h, want_dt)
+
+    def advance_to(self, t_end: float, max_steps: int = 1 << 40):
+        return hydro_advance_to(self.h, t_end, max_steps)
+
+    def run_steps(self, n: int):
+        """n free steps (no t_end clamp) without synchronising."""
+        for _ in range(n):
+            hydro_step(self.h, False)
+
+    # reductions -------------------------------------------------------
+    def totals(self) -> np.ndarray:
+        return hydro_reduce(self.h, HYDRO_RED_TOTALS, self.prob.nvar)
+
+    @property
+    def dt(self) -> float:
+        return float(hydro_reduce(self.h, HYDRO_RED_DT)[0])
+
+    @property
+    def t(self) -> float:
+        return float(hydro_reduce(self.h, HYDRO_RED_TIME)[0])
+
+    @property
+    def nstep(self) -> int:
+        return int(hydro_reduce(self.h, HYDRO_RED_STEP)[0])
+
+    @property
+    def dt_last(self) -> float:
+        return float(hydro_reduce(self.h, HYDRO_RED_DT_LAST)[0])
+
+    @property
+    def max_speed(self) -> float:
+        return float(hydro_reduce(self.h, HYDRO_RED_MAXSPEED)[0])
+
+    # fields -----------------------------------------------------------
+    def conserved(self) -> np.ndarray:
+        out = np.empty(self.prob.shape, dtype=np.float64)
+        hydro_get_fields(self.h, 0, out)
+        return out
+
+    def primitive(self) -> np.ndarray:
+        out = np.empty(self.prob.shape, dtype=np.float64)
+        hydro_get_fields(self.h, 1, out)
+        return out
+
+    def get_state(self) -> np.ndarray:
+        dt = np.float32 if self.prob.precision == inputs.FP32 else np.float64
+        out = np.empty(self.prob.shape, dtype=dt)
+        hydro_get_state(self.h, out)
+        return out
+
+    def set_state(self, raw: np.ndarray, t: float, step: int):
+        raw = np.ascontiguousarray(raw)
+        if raw.nbytes != self.state_bytes:
+            raise ValueError("state size mismatch")
+        hydro_set_state(self.h, raw, t, step)
+
+    def current_ptr(self) -> int:
+        return hydro_current(self.h)
+
+    def launches(self) -> int:
+        return hydro_launch_count(self.h)
+
+    def set_zchunk(self, z: int):
+        hydro_set_zchunk(self.h, z)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            hydro_destroy(self.h)
+            self.h = None
+        self._bufs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
