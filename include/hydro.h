@@ -152,6 +152,29 @@ long hydro_launch_count(hydro_sim *sim);
 int hydro_destroy(hydro_sim *sim);
 const char *hydro_strerror(int status);
 
+/* Conserved totals of a state without any allocation.  The paper has no
+   counterpart to this call; it exists for callers that must not allocate
+   device memory themselves, e.g. a host application whose memory manager has
+   already reserved the device's memory for its own pool (a cudaMalloc would
+   fail or fragment that pool), or a time-critical loop that cannot afford the
+   device-wide synchronisation that cudaMalloc and cudaFree can cause.
+   It computes the same FP64 fixed-order sums as hydro_reduce with
+   HYDRO_RED_TOTALS (out[q] = sum over cells of the total conserved variable q
+   times the cell volume, q < ndim + 2) for the state U (device pointer, the
+   layout and precision of prob; with hse_subtract the stored perturbation,
+   and bg the HOST background tables in hydro_init's order).  Its scratch is
+   one fixed array of about 420 KB in device memory, part of the library
+   image: every GPU that loads the library holds it until the process exits.
+   Limits: hse problems need nz + 5 <= 4096; larger ones are rejected with
+   HYDRO_ERR_INVALID_ARG before anything is launched.  The first call on each
+   device looks up the array's device address (with that device current);
+   make that first call before any stream capture.  All calls share the one
+   array: calls whose work overlaps on the GPU (other streams or threads)
+   race and give wrong sums; calls on one stream are ordered.  Runs on
+   `stream` and synchronises it; calls no allocating routine. */
+int hydro_totals_noalloc(const hydro_problem *prob, const void *U, const double *bg,
+                         void *stream, double *out);
+
 #ifdef __cplusplus
 }
 #endif

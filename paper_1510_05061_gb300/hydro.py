@@ -44,7 +44,7 @@ EXPORTS = (
     "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_step",
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
     "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk",
-    "hydro_launch_count", "hydro_destroy", "hydro_strerror",
+    "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
 )
 
 
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH):
     L.hydro_destroy.argtypes = [vp]
     L.hydro_strerror.restype = C.c_char_p
     L.hydro_strerror.argtypes = [C.c_int]
+    L.hydro_totals_noalloc.restype = C.c_int
+    L.hydro_totals_noalloc.argtypes = [P, vp, D, vp, D]
     _lib = L
     return L
 
@@ -225,6 +227,15 @@ def hydro_launch_count(h) -> int:
 
 def hydro_destroy(h):
     _check(load().hydro_destroy(h), "hydro_destroy")
+
+
+def hydro_totals_noalloc(prob: hydro_problem, U: int, bg: Optional[np.ndarray], stream: int,
+                         nvar: int) -> np.ndarray:
+    """Totals of the device state U with no allocation (see include/hydro.h)."""
+    out = np.zeros(nvar, dtype=np.float64)
+    _check(load().hydro_totals_noalloc(C.byref(prob), C.c_void_p(U), _dptr(bg), C.c_void_p(stream),
+                                       _dptr(out)), "hydro_totals_noalloc")
+    return out
 
 
 # --------------------------------------------------------------- wrapper
