@@ -27,6 +27,7 @@ struct hydro_sim {
     Ctrl *ctrl;
     double *partial;
     PlaneBG *bg;
+    PlaneBGT<float> *bgf;
     cudaStream_t stream;
     double dx[3], inv_dx[3], cell_volume;
     int tiles_x, tiles_y;
@@ -34,6 +35,7 @@ struct hydro_sim {
     long launches;
     int err_state;           // sticky host-side copy of a non-physical error
     std::vector<PlaneBG> bg_host;
+    std::vector<PlaneBGT<float>> bgf_host;
 };
 
 namespace {
@@ -98,6 +100,8 @@ WorkLayout layout(const hydro_problem *p)
     off = align_up(off + sizeof(double) * (size_t)nparts);
     L.bg = off;
     off = align_up(off + (p->hse_subtract ? sizeof(PlaneBG) * (size_t)(p->n[2] + 5) : 0));
+    L.bgf = off;
+    off = align_up(off + (p->hse_subtract ? sizeof(PlaneBGT<float>) * (size_t)(p->n[2] + 5) : 0));
     L.red = off;
     L.total = off;
     return L;
@@ -156,7 +160,10 @@ StepArgs step_args(const hydro_sim *s, double t_end)
     a.t_end = t_end;
     a.ctrl = s->ctrl;
     a.partial = s->partial;
-    a.bg = s->prob.hse_subtract ? s->bg : nullptr;
+    a.bgT = nullptr;
+    if (s->prob.hse_subtract)
+        a.bgT = s->prob.precision == HYDRO_FP32 ? static_cast<const void *>(s->bgf)
+                                                : static_cast<const void *>(s->bg);
     a.zchunk = s->zchunk;
     a.tiles_x = s->tiles_x;
     return a;
@@ -263,6 +270,7 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
     s->ctrl = reinterpret_cast<Ctrl *>(s->work + s->lay.ctrl);
     s->partial = reinterpret_cast<double *>(s->work + s->lay.partial);
     s->bg = reinterpret_cast<PlaneBG *>(s->work + s->lay.bg);
+    s->bgf = reinterpret_cast<PlaneBGT<float> *>(s->work + s->lay.bgf);
     s->stream = static_cast<cudaStream_t>(stream);
     s->cell_volume = 1.0;
     for (int d = 0; d < 3; ++d) {
@@ -307,6 +315,16 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
             }
         }
         e = cudaMemcpyAsync(s->bg, s->bg_host.data(), sizeof(PlaneBG) * s->bg_host.size(),
+                            cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) { delete s; return HYDRO_ERR_CUDA; }
+        // the same constants rounded once to FP32 for the FP32 step
+        s->bgf_host.resize(s->bg_host.size());
+        for (size_t i = 0; i < s->bg_host.size(); ++i) {
+            const PlaneBG &b = s->bg_host[i];
+            s->bgf_host[i] = PlaneBGT<float>{(float)b.rho_c, (float)b.p_c, (float)b.rho_f, (float)b.p_f,
+                                             (float)b.drho, (float)b.dp, (float)b.B, 0.0f};
+        }
+        e = cudaMemcpyAsync(s->bgf, s->bgf_host.data(), sizeof(PlaneBGT<float>) * s->bgf_host.size(),
                             cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) { delete s; return HYDRO_ERR_CUDA; }
     }

@@ -37,13 +37,41 @@ __device__ __forceinline__ int map_index(int g, int n, int bclo, int bchi, bool 
     return min(max(g, 0), n - 1);
 }
 
+// Reciprocal square root, quotient and reciprocal in the working precision.
+// FP64 uses CUDA's IEEE-accurate double routines; FP32 uses the SFU
+// approximations (rsqrtf, __fdividef: at most 2 ulp), well inside the FP32
+// path's error budget.
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+
+// x > 0 (false for +-0 and for negative values).  For doubles the test is
+// an integer test of the bit pattern, which keeps it off the FP64 pipe.
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+
 // MC limiter (van Leer 1977): full-cell slope sign(dr) min(2|dl|, 2|dr|,
 // |dl+dr|/2) when dl and dr have the same sign, else 0.
-template <typename T>
-__device__ __forceinline__ T mc_slope(T dl, T dr)
+__device__ __forceinline__ float mc_slope(float dl, float dr)
 {
-    T a = fmin(fmin(T(2) * fabs(dl), T(2) * fabs(dr)), T(0.5) * fabs(dl + dr));
-    return (dl * dr > T(0)) ? copysign(a, dr) : T(0);
+    const float a = fminf(2.0f * fminf(fabsf(dl), fabsf(dr)), 0.5f * fabsf(dl + dr));
+    return (dl * dr > 0.0f) ? copysignf(a, dr) : 0.0f;
+}
+
+// FP64 form: the sign test and both minima act on the IEEE bit patterns
+// (for non-negative doubles integer order equals numeric order), leaving
+// three FP64 operations per slope: 2 min(|dl|,|dr|), dl + dr and the halving.
+__device__ __forceinline__ double mc_slope(double dl, double dr)
+{
+    const long long bl = __double_as_longlong(dl), br = __double_as_longlong(dr);
+    const long long al = bl & 0x7fffffffffffffffll, ar = br & 0x7fffffffffffffffll;
+    const bool same = ((bl ^ br) >= 0) && al != 0 && ar != 0;
+    const double m = __longlong_as_double(min(al, ar));
+    const double twice = m + m;
+    const double half_sum = 0.5 * fabs(dl + dr);
+    const double a = __longlong_as_double(min(__double_as_longlong(twice), __double_as_longlong(half_sum)));
+    return same ? copysign(a, dr) : 0.0;
 }
 
 // Background seen by one cell in HSE mode (all zero in plain mode).
@@ -56,16 +84,16 @@ struct CellBG {
 };
 
 template <typename T, bool HSE>
-__device__ __forceinline__ CellBG<T> cell_bg(const PlaneBG *bg, int k)
+__device__ __forceinline__ CellBG<T> cell_bg(const PlaneBGT<T> *bg, int k)
 {
     CellBG<T> b;
     if constexpr (HSE) {
-        const PlaneBG &c = bg[k + 2];
-        const PlaneBG &u = bg[k + 3];
-        b.rho = T(c.rho_c); b.p = T(c.p_c);
-        b.drho = T(c.drho); b.dp = T(c.dp); b.B = T(c.B);
-        b.rho_lo = T(c.rho_f); b.p_lo = T(c.p_f);
-        b.rho_hi = T(u.rho_f); b.p_hi = T(u.p_f);
+        const PlaneBGT<T> &c = bg[k + 2];
+        const PlaneBGT<T> &u = bg[k + 3];
+        b.rho = c.rho_c; b.p = c.p_c;
+        b.drho = c.drho; b.dp = c.dp; b.B = c.B;
+        b.rho_lo = c.rho_f; b.p_lo = c.p_f;
+        b.rho_hi = u.rho_f; b.p_hi = u.p_f;
     } else {
         b.rho = b.p = b.drho = b.dp = b.B = T(0);
         b.rho_lo = b.p_lo = b.rho_hi = b.p_hi = T(0);
@@ -124,7 +152,7 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
         const T r_hi = rb_hi + (wh[0] + T(0.5) * dw[d][0]);
         const T p_lo = pb_lo + (wh[NV - 1] - T(0.5) * dw[d][NV - 1]);
         const T p_hi = pb_hi + (wh[NV - 1] + T(0.5) * dw[d][NV - 1]);
-        ok = ok && (r_lo > T(0)) && (r_hi > T(0)) && (p_lo > T(0)) && (p_hi > T(0));
+        ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
     }
     if (!ok) {
 #pragma unroll
@@ -144,10 +172,16 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
 // wl, wr hold (rho', u, p') and (rb, pb) the background at the face; in plain
 // mode rb = pb = 0.  The normal momentum flux carries p' (= p in plain mode).
 // Branches: 0 <= S_L -> F_L; S_L < 0 <= S* -> F*_L; S* < 0 < S_R -> F*_R;
-// S_R <= 0 -> F_R.
+// S_R <= 0 -> F_R.  igm1 = 1/(gamma - 1).
+//
+// Arithmetic is arranged to need two square-root reciprocals and two
+// divisions per face: c = g rsqrt(g rho) with g = gamma p, and with
+// q = 1/(S_K - S*) the star state U*_K = q (rho_K (S_K - u_K)) [1, S*, v_t]
+// and E*_K = q [(S_K - u_K) E_K + (S* - u_K)(rho_K (S_K - u_K) S* + p_K)],
+// which is the star state of Toro eq. (10.39) multiplied out.
 template <typename T, int ND, int D, bool HSE>
 __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2], T rb, T pb,
-                                     T gam, T (&f)[ND + 2])
+                                     T gam, T igm1, T (&f)[ND + 2])
 {
     constexpr int NV = ND + 2;
     const T rl = HSE ? rb + wl[0] : wl[0];
@@ -155,8 +189,9 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     const T pl = HSE ? pb + wl[NV - 1] : wl[NV - 1];
     const T pr = HSE ? pb + wr[NV - 1] : wr[NV - 1];
     const T ul = wl[1 + D], ur = wr[1 + D];
-    const T cl = sqrt(gam * pl / rl);
-    const T cr = sqrt(gam * pr / rr);
+    const T gpl = gam * pl, gpr = gam * pr;
+    const T cl = gpl * rsqrt_t(gpl * rl);
+    const T cr = gpr * rsqrt_t(gpr * rr);
     const T sl = fmin(ul - cl, ur - cr);
     const T sr = fmax(ul + cl, ur + cr);
 
@@ -167,7 +202,8 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     else {
         // pressure difference from the perturbations: the background cancels
         const T dpp = wr[NV - 1] - wl[NV - 1];
-        sstar = (dpp + rl * ul * (sl - ul) - rr * ur * (sr - ur)) / (rl * (sl - ul) - rr * (sr - ur));
+        const T ml = rl * (sl - ul), mr = rr * (sr - ur);
+        sstar = div_t(dpp + ml * ul - mr * ur, ml - mr);
         left = sstar >= T(0);
         star = true;
     }
@@ -182,7 +218,7 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     T ke = T(0);
 #pragma unroll
     for (int e = 0; e < ND; ++e) ke += vk[e] * vk[e];
-    const T Ek = pk / (gam - T(1)) + T(0.5) * rk * ke;
+    const T Ek = pk * igm1 + T(0.5) * rk * ke;
 
     // Euler flux of the chosen side
     const T mflux = rk * uk;
@@ -193,9 +229,12 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     f[NV - 1] = uk * (Ek + pk);
 
     if (star) {
-        // F*_K = F_K + S_K (U*_K - U_K), U*_K from Toro eq. (10.39)
-        const T fac = rk * (sk - uk) / (sk - sstar);
-        const T e_star = fac * (Ek / rk + (sstar - uk) * (sstar + pk / (rk * (sk - uk))));
+        // F*_K = F_K + S_K (U*_K - U_K)
+        const T skmu = sk - uk;
+        const T q = div_t(T(1), sk - sstar);
+        const T mk = rk * skmu;
+        const T fac = mk * q;
+        const T e_star = q * (skmu * Ek + (sstar - uk) * (mk * sstar + pk));
         f[0] += sk * (fac - rk);
 #pragma unroll
         for (int e = 0; e < ND; ++e) {

@@ -25,15 +25,18 @@ struct __align__(16) Ctrl {
     double pad[2];
 };
 
-// Per z-plane background constants of the hydrostatic-background mode, FP64,
-// for planes k = -2 .. nz+2 (entry k + 2).
-struct PlaneBG {
-    double rho_c, p_c;  // background at the plane centre (0 for k = nz+2)
-    double rho_f, p_f;  // background at the plane's low face z_lo + k dz
-    double drho, dp;    // face(k+1) - face(k) (0 for k = nz+2)
-    double B;           // (p_f(k+1) - p_f(k))/dz - rho_c g_z: discrete imbalance
-    double pad;
+// Per z-plane background constants of the hydrostatic-background mode for
+// planes k = -2 .. nz+2 (entry k + 2).  Computed in FP64 on the host; the
+// FP32 step reads a float copy so that no per-cell conversion is needed.
+template <typename T>
+struct PlaneBGT {
+    T rho_c, p_c;   // background at the plane centre (0 for k = nz+2)
+    T rho_f, p_f;   // background at the plane's low face z_lo + k dz
+    T drho, dp;     // face(k+1) - face(k) (0 for k = nz+2)
+    T B;            // (p_f(k+1) - p_f(k))/dz - rho_c g_z: discrete imbalance
+    T pad;
 };
+using PlaneBG = PlaneBGT<double>;
 
 // Arguments of one step launch (passed by value).
 struct StepArgs {
@@ -49,14 +52,14 @@ struct StepArgs {
     double t_end;       // clamp target (+inf for a free step)
     Ctrl *ctrl;
     double *partial;    // per-CTA max signal speed
-    const PlaneBG *bg;  // hse tables (nullptr in plain mode)
+    const void *bgT;    // hse tables in the step's precision (nullptr in plain mode)
     int zchunk;         // planes per CTA (3D)
     int tiles_x;        // tiles along x
 };
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WorkLayout {
-    size_t ctrl, partial, bg, red, total;
+    size_t ctrl, partial, bg, bgf, red, total;
     int max_ctas;
 };
 

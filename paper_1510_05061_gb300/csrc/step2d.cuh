@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
     const T gam = T(a.gamma);
+    const T igm1 = T(1.0 / (a.gamma - 1.0));
     const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(0)};
     const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(0)};
 
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     }
     __syncthreads();
 
-    const CellBG<T> nobg = cell_bg<T, false>(nullptr, 0);
+    const CellBG<T> nobg = cell_bg<T, false>(static_cast<const PlaneBGT<T> *>(nullptr), 0);
     auto predict = [&](int cx, int cy, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
         const int hx = cx + 2, hy = cy + 2;
 #pragma unroll
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
         const int gf = x0 + fi;
         if (gf == 0 && a.bc_lo[0] == BC_REFLECT) mirror_state<T, NV, 0>(wr, wl);
         if (gf == nx && a.bc_hi[0] == BC_REFLECT) mirror_state<T, NV, 0>(wl, wr);
-        hllc<T, ND, 0, false>(wl, wr, T(0), T(0), gam, f);
+        hllc<T, ND, 0, false>(wl, wr, T(0), T(0), gam, igm1, f);
 #pragma unroll
         for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
     }
@@ -172,14 +173,14 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
         const int gf = y0 + fi;
         if (gf == 0 && a.bc_lo[1] == BC_REFLECT) mirror_state<T, NV, 1>(wr, wl);
         if (gf == ny && a.bc_hi[1] == BC_REFLECT) mirror_state<T, NV, 1>(wl, wr);
-        hllc<T, ND, 1, false>(wl, wr, T(0), T(0), gam, f);
+        hllc<T, ND, 1, false>(wl, wr, T(0), T(0), gam, igm1, f);
 #pragma unroll
         for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
     }
     __syncthreads();
 
     // ---- update, admissibility, CFL signal speed
-    double smax = 0.0;
+    T smax = T(0);
     bool bad = false;
     if (own) {
         const size_t c = (size_t)gy * nx + gx;
@@ -204,13 +205,14 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
         const T rinv = T(1) / u[0];
         const T vx = u[1] * rinv, vy = u[2] * rinv;
         const T pres = (gam - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
-        const T cs = sqrt(gam * pres * rinv);
+        const T gp = gam * pres;
+        const T cs = gp * rsqrt_t(gp * u[0]);
         const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1];
         if (!(u[0] > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
-        else smax = double(s);
+        else smax = s;
     }
     const bool bad_cta = __syncthreads_or(bad) != 0;
-    const double m = block_max<NT>(smax, red);
+    const double m = block_max<NT>(double(smax), red);
     finish_step<NT>(m, bad_cta, a, nblocks, dtd, true, &s_last);
 }
 

@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
     const T gam = T(a.gamma);
+    const T igm1 = T(1.0 / (a.gamma - 1.0));
+    const PlaneBGT<T> *bgT = static_cast<const PlaneBGT<T> *>(a.bgT);
     const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(a.inv_dx[2])};
     const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(a.grav[2])};
 
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
         const int slot = (pz + 3) % 3;
         bool fz;
         const int gz = map_index(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
-        const T rho_bg = HSE ? T(a.bg[pz + 2].rho_c) : T(0);
+        const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
         for (int i = tid; i < HX * HY; i += NT) {
             const int hx = i % HX, hy = i / HX;
             bool fx, fy;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
             dw[1][q] = mc_slope(c - P(s0, q, hy - 1, hx), P(s0, q, hy + 1, hx) - c);
             dw[2][q] = mc_slope(c - P(sm, q, hy, hx), P(sp, q, hy, hx) - c);
         }
-        const CellBG<T> bg = cell_bg<T, HSE>(a.bg, p);
+        const CellBG<T> bg = cell_bg<T, HSE>(bgT, p);
         hancock<T, ND, HSE>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
     };
 
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
     T msrc_prev = T(0);
 #pragma unroll
     for (int q = 0; q < NV; ++q) { ztop_prev[q] = T(0); fz_prev[q] = T(0); div_prev[q] = T(0); }
-    double smax = 0.0;
+    T smax = T(0);
     bool bad = false;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
@@ -208,8 +210,8 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
         __syncthreads();
 
         // ---- step 3: face fluxes
-        const T rb_c = HSE ? T(a.bg[p + 2].rho_c) : T(0);
-        const T pb_c = HSE ? T(a.bg[p + 2].p_c) : T(0);
+        const T rb_c = HSE ? bgT[p + 2].rho_c : T(0);
+        const T pb_c = HSE ? bgT[p + 2].p_c : T(0);
         if (xy) {
             for (int i = tid; i < (TX + 1) * TY; i += NT) {
                 const int fi = i % (TX + 1), cy = i / (TX + 1);
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
                 const int gf = x0 + fi;
                 if (gf == 0 && a.bc_lo[0] == BC_REFLECT) mirror_state<T, NV, 0>(wr, wl);
                 if (gf == nx && a.bc_hi[0] == BC_REFLECT) mirror_state<T, NV, 0>(wl, wr);
-                hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, f);
+                hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
             }
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
                 const int gf = y0 + fi;
                 if (gf == 0 && a.bc_lo[1] == BC_REFLECT) mirror_state<T, NV, 1>(wr, wl);
                 if (gf == ny && a.bc_hi[1] == BC_REFLECT) mirror_state<T, NV, 1>(wl, wr);
-                hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, f);
+                hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
             }
@@ -252,9 +254,9 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
 #pragma unroll
                 for (int q = 0; q < NV; ++q) { wl[q] = ztop_prev[q]; wr[q] = zlo[q]; }
             }
-            const T rb_f = HSE ? T(a.bg[p + 2].rho_f) : T(0);
-            const T pb_f = HSE ? T(a.bg[p + 2].p_f) : T(0);
-            hllc<T, ND, 2, HSE>(wl, wr, rb_f, pb_f, gam, fz);
+            const T rb_f = HSE ? bgT[p + 2].rho_f : T(0);
+            const T pb_f = HSE ? bgT[p + 2].p_f : T(0);
+            hllc<T, ND, 2, HSE>(wl, wr, rb_f, pb_f, gam, igm1, fz);
         } else {
 #pragma unroll
             for (int q = 0; q < NV; ++q) fz[q] = T(0);
@@ -279,22 +281,23 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 T src = grav[d] * rsum;
-                if (HSE && d == 2) src -= T(a.bg[k + 2].B);
+                if (HSE && d == 2) src -= bgT[k + 2].B;
                 u[1 + d] += dt * (du[1 + d] + src);
             }
             u[4] += dt * (du[4] + msrc);
 #pragma unroll
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
             // CFL signal speed and admissibility of the new state
-            const T rho = HSE ? T(a.bg[k + 2].rho_c) + u[0] : u[0];
+            const T rho = HSE ? bgT[k + 2].rho_c + u[0] : u[0];
             const T rinv = T(1) / rho;
             const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
             const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
-            const T pres = HSE ? T(a.bg[k + 2].p_c) + pp : pp;
-            const T cs = sqrt(gam * pres * rinv);
+            const T pres = HSE ? bgT[k + 2].p_c + pp : pp;
+            const T gp = gam * pres;
+            const T cs = gp * rsqrt_t(gp * rho);
             const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
             if (!(rho > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
-            else smax = fmax(smax, double(s));
+            else smax = fmax(smax, s);
         }
         if (xy) {
             T dv[NV];
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
     }
 
     const bool bad_cta = __syncthreads_or(bad) != 0;
-    const double m = block_max<NT>(smax, red);
+    const double m = block_max<NT>(double(smax), red);
     finish_step<NT>(m, bad_cta, a, nblocks, dtd, true, &s_last);
 }
 
