@@ -38,12 +38,15 @@ from paper_1510_05061_gb300 import inputs  # noqa: E402
 METRIC = "zone-updates/s"
 UNIT = "zone-updates/s"
 
-# Algorithmic work per zone-update of the fused 3D step:
-# bytes = read U^n once + write U^{n+1} once = 2 * nvar * sizeof(T);
-# FP64 operations counted once per cell and once per face (three faces per
-# cell), divisions and square roots counted as one operation each.
-FLOPS_PER_ZONE_3D = 612
-FLOPS_PER_ZONE_2D = 350
+# Algorithmic work per zone-update of the fused step: bytes = read U^n once +
+# write U^{n+1} once = 2 * nvar * sizeof(T); floating-point operations of the
+# scheme counted once per cell and once per face (ndim faces per cell),
+# divisions, square roots and min/max counted as one operation each:
+# 3D = primitives 13 + MC slopes 75 + half step 83 + face states 60 +
+#      3 HLLC x 72 + update 70 + CFL speed 25 = 542;
+# 2D = 10 + 40 + 50 + 32 + 2 x 64 + 42 + 19 = 321.
+FLOPS_PER_ZONE_3D = 542
+FLOPS_PER_ZONE_2D = 321
 
 CONFIGS = {
     # name: (builder, description, precision, hse)

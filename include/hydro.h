@@ -149,6 +149,14 @@ int hydro_set_zchunk(hydro_sim *sim, int zchunk);
 /* Number of kernels launched by this handle so far. */
 long hydro_launch_count(hydro_sim *sim);
 
+/* Test hook: evaluate the update's FP64 arithmetic helpers on n device
+   values, out[i] = 1/x[i] (which = 0), y[i]/x[i] (1), 1/sqrt(x[i]) (2) or
+   the MC-limited slope of (x[i], y[i]) (3), so that they can be checked
+   against CUDA's IEEE operations.  x, y, out: device pointers.  Synchronises
+   the stream. */
+int hydro_selftest_math(int which, const double *x, const double *y, double *out, long n,
+                        void *stream);
+
 int hydro_destroy(hydro_sim *sim);
 const char *hydro_strerror(int status);
 

@@ -210,6 +210,18 @@ __global__ void fields_kernel(const AuxArgs a, double *__restrict__ out, long lo
     }
 }
 
+__global__ void math_kernel(int which, const double *__restrict__ x, const double *__restrict__ y,
+                            double *__restrict__ out, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (which == 0) out[i] = rcp_t(x[i]);
+        else if (which == 1) out[i] = div_t(y[i], x[i]);
+        else if (which == 2) out[i] = rsqrt_t(x[i]);
+        else out[i] = mc_slope(x[i], y[i]);
+    }
+}
+
 template <typename T>
 __global__ void poke_kernel(const AuxArgs a, int var, long long cell, double v)
 {
@@ -270,6 +282,13 @@ cudaError_t launch_fields(const AuxArgs &a, double *staging, long long c0, long 
                           cudaStream_t s)
 {
     HYDRO_DISPATCH(fields_kernel, grid_for(m), 256, s, a, staging, c0, m, what);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_math(int which, const double *x, const double *y, double *out, long long n,
+                        cudaStream_t s)
+{
+    math_kernel<<<grid_for(n), 256, 0, s>>>(which, x, y, out, n);
     return cudaGetLastError();
 }
 

@@ -487,6 +487,16 @@ int hydro_set_zchunk(hydro_sim *s, int zchunk)
 
 long hydro_launch_count(hydro_sim *s) { return s ? s->launches : -1; }
 
+int hydro_selftest_math(int which, const double *x, const double *y, double *out, long n, void *stream)
+{
+    if (which < 0 || which > 3 || !x || !out || n < 0 || ((which == 1 || which == 3) && !y))
+        return HYDRO_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_math(which, x, y, out, n, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_status(e);
+}
+
 int hydro_destroy(hydro_sim *s)
 {
     if (!s) return HYDRO_ERR_INVALID_ARG;

@@ -43,7 +43,25 @@ __device__ __forceinline__ int map_index(int g, int n, int bclo, int bchi, bool 
 // path's error budget.
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+
+// FP64 reciprocal by Newton-Raphson iteration on f(y) = 1/y - b, which
+// doubles the number of correct bits per step: y <- y + y (1 - b y).  The
+// start value is the hardware approximation rcp.approx.ftz.f64 (about 20
+// correct bits), so two steps reach the FP64 rounding level; the result is
+// within a couple of ulp of 1/b for normal b (not always correctly rounded),
+// far inside the 1e-10 parity budget.  Costs one SFU operation and four
+// FMAs on the FP64 pipe.
+__device__ __forceinline__ double rcp_t(double b)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(b));
+    double e = fma(-b, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-b, y, 1.0);
+    return fma(y, e, y);
+}
+__device__ __forceinline__ float rcp_t(float b) { return __fdividef(1.0f, b); }
+__device__ __forceinline__ double div_t(double a, double b) { return a * rcp_t(b); }
 __device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
 
 // x > 0 (false for +-0 and for negative values).  For doubles the test is
@@ -114,7 +132,7 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     constexpr int NV = ND + 2;
     const T rho = HSE ? bg.rho + w[0] : w[0];
     const T pr = HSE ? bg.p + w[NV - 1] : w[NV - 1];
-    const T rinv = T(1) / rho;
+    const T rinv = rcp_t(rho);
     T rate[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) rate[q] = T(0);
@@ -231,7 +249,7 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     if (star) {
         // F*_K = F_K + S_K (U*_K - U_K)
         const T skmu = sk - uk;
-        const T q = div_t(T(1), sk - sstar);
+        const T q = rcp_t(sk - sstar);
         const T mk = rk * skmu;
         const T fac = mk * q;
         const T e_star = q * (skmu * Ek + (sstar - uk) * (mk * sstar + pk));

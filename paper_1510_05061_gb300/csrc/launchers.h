@@ -42,6 +42,9 @@ cudaError_t launch_totals(const AuxArgs &a, cudaStream_t s);
 // (what = 1) variables in staging (planes of length m)
 cudaError_t launch_fields(const AuxArgs &a, double *staging, long long c0, long long m,
                           int what, cudaStream_t s);
+// device arithmetic helpers over n values (0: 1/x, 1: y/x, 2: 1/sqrt(x), 3: MC slope of (x, y))
+cudaError_t launch_math(int which, const double *x, const double *y, double *out, long long n,
+                        cudaStream_t s);
 // one stored value
 cudaError_t launch_poke(const AuxArgs &a, int var, long long cell, double v, cudaStream_t s);
 

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
         const T e = U[c + 3 * vs];
         if (fx) m0 = -m0;
         if (fy) m1 = -m1;
-        const T rinv = T(1) / r;
+        const T rinv = rcp_t(r);
         P(0, hy, hx) = r;
         P(1, hy, hx) = m0 * rinv;
         P(2, hy, hx) = m1 * rinv;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
         u[3] += dt * (du[3] + msrc);
 #pragma unroll
         for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
-        const T rinv = T(1) / u[0];
+        const T rinv = rcp_t(u[0]);
         const T vx = u[1] * rinv, vy = u[2] * rinv;
         const T pres = (gam - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
         const T gp = gam * pres;

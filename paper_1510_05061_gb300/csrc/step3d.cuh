@@ -37,9 +37,12 @@ struct Step3DSmem {
 };
 
 template <typename T, bool HSE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1) step3d_kernel(const StepArgs a)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
+    // FP32 keeps the next plane's loads in flight; FP64 is bound by its
+    // arithmetic pipe and has no registers to spare for them
+    constexpr bool PREFETCH = sizeof(T) == 4;
     using S = Step3DSmem<T, HSE, TX, TY>;
     constexpr int HX = S::HX, HY = S::HY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -87,31 +90,51 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
         return prim[((size_t)(slot * NV + q) * HY + hy) * HX + hx];
     };
 
-    // ---- stage plane pz (may be a ghost plane) into ring slot
-    auto load_plane = [&](int pz) {
-        const int slot = (pz + 3) % 3;
+    // ---- stage plane pz (may be a ghost plane) into its ring slot, in two
+    // halves: fetch() issues the global loads (boundary conditions applied
+    // by index mapping, mirrored momenta negated) into registers, store()
+    // converts them to primitives in shared memory.  With PREFETCH the fetch
+    // of plane p+2 is in flight while plane p is computed.
+    constexpr int NLOAD = (HX * HY + NT - 1) / NT;
+    T raw[NLOAD][NV];
+    auto fetch = [&](int pz) {
         bool fz;
         const int gz = map_index(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
+#pragma unroll
+        for (int j = 0; j < NLOAD; ++j) {
+            const int i = tid + j * NT;
+            if (i < HX * HY) {
+                const int hx = i % HX, hy = i / HX;
+                bool fx, fy;
+                const int gx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
+                const int gy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
+                const size_t c = (size_t)gz * a.plane + (size_t)gy * nx + gx;
+                raw[j][0] = U[c];
+                const T m0 = U[c + vs], m1 = U[c + 2 * vs], m2 = U[c + 3 * vs];
+                raw[j][1] = fx ? -m0 : m0;
+                raw[j][2] = fy ? -m1 : m1;
+                raw[j][3] = fz ? -m2 : m2;
+                raw[j][4] = U[c + 4 * vs];
+            }
+        }
+    };
+    auto store = [&](int pz) {
+        const int slot = (pz + 3) % 3;
         const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
-        for (int i = tid; i < HX * HY; i += NT) {
-            const int hx = i % HX, hy = i / HX;
-            bool fx, fy;
-            const int gx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
-            const int gy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
-            const size_t c = (size_t)gz * a.plane + (size_t)gy * nx + gx;
-            const T r = U[c];
-            T m0 = U[c + vs], m1 = U[c + 2 * vs], m2 = U[c + 3 * vs];
-            const T e = U[c + 4 * vs];
-            if (fx) m0 = -m0;
-            if (fy) m1 = -m1;
-            if (fz) m2 = -m2;
-            const T rho = HSE ? rho_bg + r : r;
-            const T rinv = T(1) / rho;
-            P(slot, 0, hy, hx) = r;
-            P(slot, 1, hy, hx) = m0 * rinv;
-            P(slot, 2, hy, hx) = m1 * rinv;
-            P(slot, 3, hy, hx) = m2 * rinv;
-            P(slot, 4, hy, hx) = (gam - T(1)) * (e - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+#pragma unroll
+        for (int j = 0; j < NLOAD; ++j) {
+            const int i = tid + j * NT;
+            if (i < HX * HY) {
+                const int hx = i % HX, hy = i / HX;
+                const T r = raw[j][0], m0 = raw[j][1], m1 = raw[j][2], m2 = raw[j][3];
+                const T rho = HSE ? rho_bg + r : r;
+                const T rinv = rcp_t(rho);
+                P(slot, 0, hy, hx) = r;
+                P(slot, 1, hy, hx) = m0 * rinv;
+                P(slot, 2, hy, hx) = m1 * rinv;
+                P(slot, 3, hy, hx) = m2 * rinv;
+                P(slot, 4, hy, hx) = (gam - T(1)) * (raw[j][4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+            }
         }
     };
 
@@ -150,10 +173,19 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
 
-    load_plane(z0 - 2);
-    load_plane(z0 - 1);
+    fetch(z0 - 2);
+    store(z0 - 2);
+    fetch(z0 - 1);
+    store(z0 - 1);
+    if constexpr (PREFETCH) fetch(z0);
     for (int p = z0 - 1; p <= z1; ++p) {
-        load_plane(p + 1);
+        if constexpr (PREFETCH) {
+            store(p + 1);
+            if (p + 2 <= z1 + 1) fetch(p + 2);
+        } else {
+            fetch(p + 1);
+            store(p + 1);
+        }
         __syncthreads();
         const bool xy = (p >= z0 && p < z1);
 
@@ -289,7 +321,7 @@ __global__ void __launch_bounds__(TX * TY, 1) step3d_kernel(const StepArgs a)
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
             // CFL signal speed and admissibility of the new state
             const T rho = HSE ? bgT[k + 2].rho_c + u[0] : u[0];
-            const T rinv = T(1) / rho;
+            const T rinv = rcp_t(rho);
             const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
             const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
             const T pres = HSE ? bgT[k + 2].p_c + pp : pp;

@@ -45,6 +45,7 @@ EXPORTS = (
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
     "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk",
     "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
+    "hydro_selftest_math",
 )
 
 
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH):
     L.hydro_destroy.argtypes = [vp]
     L.hydro_strerror.restype = C.c_char_p
     L.hydro_strerror.argtypes = [C.c_int]
+    L.hydro_selftest_math.restype = C.c_int
+    L.hydro_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_long, vp]
     L.hydro_totals_noalloc.restype = C.c_int
     L.hydro_totals_noalloc.argtypes = [P, vp, D, vp, D]
     _lib = L
@@ -223,6 +226,11 @@ def hydro_set_zchunk(h, z: int):
 
 def hydro_launch_count(h) -> int:
     return load().hydro_launch_count(h)
+
+
+def hydro_selftest_math(which: int, x: int, y: int, out: int, n: int, stream: int):
+    _check(load().hydro_selftest_math(int(which), C.c_void_p(x), C.c_void_p(y), C.c_void_p(out),
+                                      int(n), C.c_void_p(stream)), "hydro_selftest_math")
 
 
 def hydro_destroy(h):
