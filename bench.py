@@ -176,7 +176,7 @@ def build_workload(cfg):
 
 
 # --------------------------------------------------------------- oracle
-def oracle_sample(seconds: float = 12.0, max_steps: int = 4, cfg="rt256-fp64", nz_slab=None):
+def oracle_sample(seconds: float = 10.0, max_steps: int = 1000, cfg="rt256-fp64", nz_slab=None):
     """Time the FP64 CPU oracle, as it stands, on a bounded sample of the
     workload.  Returns (zone-updates/s, cores, sample description)."""
     import oracle
