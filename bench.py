@@ -376,6 +376,39 @@ def run_gpu(args):
     return 0
 
 
+def run_precision_report(args):
+    """RT n^3 to t = 0.5 in FP32 (bulk) and FP64, both with hydrostatic-
+    background subtraction: density L1-relative difference and throughput."""
+    import torch
+
+    from paper_1510_05061_gb300 import build as hbuild
+    from paper_1510_05061_gb300 import hydro
+
+    hbuild.build()
+    n = args.precision_n
+    out = {"workload": f"Rayleigh-Taylor {n}^3, hse subtraction, t_end = {args.t_end}"}
+    rho = {}
+    for prec, name in ((inputs.FP32, "fp32"), (inputs.FP64, "fp64")):
+        prob, W = inputs.rayleigh_taylor(n, precision=prec, hse_subtract=1)
+        sim = hydro.Simulation(prob, W)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, t = sim.advance_to(args.t_end)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        P = sim.primitive()
+        rho[name] = P[0]
+        out[name] = {"steps": steps, "t": t, "seconds": el,
+                     "zone_updates_per_s": prob.ncell * steps / el}
+        sim.close()
+        del P
+    diff = float(np.abs(rho["fp32"] - rho["fp64"]).sum() / np.abs(rho["fp64"]).sum())
+    out["density_l1_rel_fp32_vs_fp64"] = diff
+    out["fp32_over_fp64_throughput"] = out["fp32"]["zone_updates_per_s"] / out["fp64"]["zone_updates_per_s"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,7 +420,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the step kernel from an ncu capture")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="FP32 vs FP64 Rayleigh-Taylor density error at t_end (no JSON bench line)")
+    ap.add_argument("--precision-n", type=int, default=512)
+    ap.add_argument("--t-end", type=float, default=0.5)
     args = ap.parse_args()
+    if args.precision_report:
+        return run_precision_report(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

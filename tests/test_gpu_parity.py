@@ -327,3 +327,19 @@ def test_fp32_rayleigh_taylor_against_fp64_oracle(hy, orc, hse):
     g = gpu_run(hy, prob.replace(precision=inputs.FP32), W, steps=40)
     err = l1rel(g["U"][0], o["U"][0])
     assert err <= 1e-5, err
+
+
+def test_fp32_rt_linear_phase_density_error(hy):
+    """FP32 bulk (FP64 dt, totals, background) against the FP64 run in the
+    same hydrostatic mode: density L1-relative difference <= 1e-3 at t = 0.5
+    (Rayleigh-Taylor 128^3, linear-growth phase)."""
+    rho = {}
+    for prec in (inputs.FP32, inputs.FP64):
+        prob, W = inputs.rayleigh_taylor(128, precision=prec, hse_subtract=1)
+        sim = hy.Simulation(prob, W)
+        n, t = sim.advance_to(0.5)
+        assert t == 0.5
+        rho[prec] = sim.primitive()[0]
+        sim.close()
+    err = l1rel(rho[inputs.FP32], rho[inputs.FP64])
+    assert err <= 1e-3, err
