@@ -58,6 +58,9 @@ CONFIGS = {
                        desc="3D Rayleigh-Taylor 512^3 FP32 bulk, FP64 dt/totals/background subtraction"),
     "rt256-fp32": dict(n=256, precision=inputs.FP32, hse=1,
                        desc="3D Rayleigh-Taylor 256^3 FP32 bulk with hydrostatic-background subtraction"),
+    "kh-batch": dict(batch=True, count=64, precision=inputs.FP32,
+                     desc="64 independent 3D periodic Kelvin-Helmholtz boxes, n log-uniform in [32, 192] "
+                          "(seed 151005062), FP32; one persistent launch per step, autotuned tiles"),
 }
 
 
@@ -171,6 +174,8 @@ def max_over_ranks(world, x: float) -> float:
 
 def build_workload(cfg):
     c = CONFIGS[cfg]
+    if c.get("batch"):
+        raise ValueError("batch configs have no single workload")
     prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
     return prob, W, c
 
@@ -252,8 +257,76 @@ def run_reference(args):
     return 0
 
 
+# -------------------------------------------------------------- batch arm
+def kh_batch_items(count=64, seed=151005062):
+    return [inputs.kelvin_helmholtz(s["n"], ndim=3, U=s["U"], ratio=s["ratio"], seed=seed,
+                                    instance=s["instance"], precision=inputs.FP32)
+            for s in inputs.kh_batch_sizes(count=count, seed=seed)]
+
+
+def run_gpu_batch(args):
+    import torch
+
+    from paper_1510_05061_gb300 import autotune
+    from paper_1510_05061_gb300 import build as hbuild
+    from paper_1510_05061_gb300 import hydro
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hydro.load()
+    c = CONFIGS[args.config]
+    items = kh_batch_items(c["count"])
+    b = hydro.Batch(items)
+    tune = autotune.tune_batch(b, use_cache=not args.retune)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    n0 = b.launches()
+    s = b.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(s)
+        b.step(args.steps)
+        ev1.record(s)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = b.launches() - n0
+    el_ms = max_over_ranks(world, ev0.elapsed_time(ev1))
+    cells = b.cells()
+    value = world * cells * args.steps / (el_ms * 1e-3)
+    per_launch_ms = el_ms / args.steps
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = 2 * 5 * 4 * cells / (per_launch_ms * 1e-3) / 1e9
+    items3, items2, grid3, grid2 = b.items()
+    b.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": c["desc"], "instances": len(items), "cells": cells,
+                       "tile": tune["tile"], "zchunk": tune["zchunk"], "work_items": items3,
+                       "persistent_grid": grid3,
+                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (cells * 20 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": args.traffic, "peak_kind": peak_kind,
+                         "kernel": "step3d_batch_kernel<float>"},
+            "autotune": {k: v for k, v in tune.items() if k != "table"},
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------- GPU arm
 def run_gpu(args):
+    if CONFIGS[args.config].get("batch"):
+        return run_gpu_batch(args)
     import torch
 
     from paper_1510_05061_gb300 import build as hbuild
@@ -420,6 +493,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the step kernel from an ncu capture")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--precision-report", action="store_true",
                     help="FP32 vs FP64 Rayleigh-Taylor density error at t_end (no JSON bench line)")
     ap.add_argument("--precision-n", type=int, default=512)

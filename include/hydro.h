@@ -160,6 +160,79 @@ int hydro_selftest_math(int which, const double *x, const double *y, double *out
 int hydro_destroy(hydro_sim *sim);
 const char *hydro_strerror(int status);
 
+/* ---------------------------------------------------------------------
+   Batched solves.  Many independent instances of different sizes (2D and
+   3D, one precision; one hydrostatic-background flag for the 3D ones) step
+   together: each step is one persistent launch over a device-resident work
+   list of (instance, tile, z-chunk) items for the 3D instances and one for
+   the 2D instances, replayed from a captured CUDA graph when the stream is
+   not the legacy default stream.  Each instance keeps its own time-control
+   block and CFL dt (the last item of an instance to finish sets it).
+   Instances may join (hydro_batch_add) and leave (hydro_batch_remove)
+   between steps; the work lists and graph are rebuilt on the next step.  The
+   paper motivates such suites as capacity computing for parameter studies
+   and uncertainty quantification ("Increasing computing power",
+   "Capabilities needed").  All buffers are caller-owned device memory,
+   256-byte aligned: per instance two state buffers (hydro_state_bytes) and
+   one instance work buffer (hydro_instance_work_bytes), plus one batch work
+   buffer (hydro_batch_create_bytes). */
+typedef struct hydro_batch hydro_batch;
+
+/* Per-instance work buffer (time control, partial slots, background
+   tables) and the largest number of work items the instance can produce. */
+size_t hydro_instance_work_bytes(const hydro_problem *prob);
+long hydro_problem_max_items(const hydro_problem *prob);
+
+/* Batch work buffer for up to max_instances instances whose work items
+   (hydro_problem_max_items summed over the 3D / the 2D instances present at
+   one time) stay within max_items3d / max_items2d. */
+size_t hydro_batch_create_bytes(int max_instances, long max_items3d, long max_items2d);
+int hydro_batch_create(int max_instances, long max_items3d, long max_items2d, int precision, void *work,
+                       void *stream, hydro_batch **out);
+
+/* Add an instance: Ua/Ub its state buffers, inst_work its work buffer, W0
+   its HOST FP64 total primitives, bg its HOST background tables (hse) or
+   NULL; it stops advancing after step_end steps (< 0: never).  *id receives
+   its index.  Returns HYDRO_ERR_OOM when max_instances or the item
+   capacity would be exceeded, HYDRO_ERR_INVALID_ARG for a precision or 3D
+   mode different from the batch's.  Synchronises. */
+int hydro_batch_add(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
+                    const double *W0, const double *bg, long step_end, int *id);
+/* Remove an instance (synchronises; its buffers are free on return). */
+int hydro_batch_remove(hydro_batch *b, int id);
+/* Graph capture on (default) or off (direct launches). */
+int hydro_batch_set_graph(hydro_batch *b, int on);
+
+/* Convenience: one work buffer of hydro_batch_workspace_bytes holding the
+   batch buffer and every instance buffer; instance i gets id i. */
+size_t hydro_batch_workspace_bytes(const hydro_problem *probs, int count);
+int hydro_batch_init(const hydro_problem *probs, int count, void *const *Ua, void *const *Ub,
+                     void *work, const double *const *W0, const double *const *bg, void *stream,
+                     hydro_batch **out);
+
+/* Select the 3D tile shape (variant index, see hydro_batch_variant_shape)
+   and the z-chunk length (0 = default); rebuilds the work lists and the
+   graph.  Results do not depend on this choice. */
+int hydro_batch_configure(hydro_batch *b, int variant, int zchunk);
+int hydro_batch_variant_shape(int variant, int *tx, int *ty);
+
+/* nsteps steps of every instance (no synchronisation). */
+int hydro_batch_step(hydro_batch *b, long nsteps);
+
+/* Per-instance reductions (HYDRO_RED_*) and FP64 field export (as
+   hydro_reduce / hydro_get_fields); both synchronise. */
+int hydro_batch_reduce(hydro_batch *b, int id, int what, double *out);
+int hydro_batch_get_fields(hydro_batch *b, int id, int what, double *host_dst);
+/* Raw stored state of an instance to HOST memory (synchronises); device
+   pointer of the buffer holding it. */
+int hydro_batch_get_state(hydro_batch *b, int id, void *host_dst);
+void *hydro_batch_current(hydro_batch *b, int id);
+
+/* Kernel launches so far; work-list sizes and persistent grid sizes. */
+long hydro_batch_launch_count(hydro_batch *b);
+int hydro_batch_items(hydro_batch *b, int *items3d, int *items2d, int *grid3d, int *grid2d);
+int hydro_batch_destroy(hydro_batch *b);
+
 /* Conserved totals of a state without any allocation.  The paper has no
    counterpart to this call; it exists for callers that must not allocate
    device memory themselves, e.g. a host application whose memory manager has

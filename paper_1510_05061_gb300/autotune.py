@@ -1,0 +1,108 @@
+"""Autotuner for the batched step: picks the 3D tile shape (TX x TY) and the
+z-chunk length (planes marched per work item) for a batch by timing real
+steps with CUDA events on the batch's stream.
+
+The choice never changes results (every tile shape and chunk length gives
+bit-identical states); it only changes speed.  Tuning advances the batch by
+the steps it times.  Choices are cached per (GPU, precision, mode, workload
+signature) in a JSON file (``HYDRO_AUTOTUNE_CACHE`` or
+~/.cache/hydro_gb300/autotune.json).
+"""
+
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Dict, Iterable, Optional
+
+from . import inputs
+
+DEFAULT_ZCHUNKS = (4, 8, 16, 32)
+
+
+def cache_path() -> str:
+    return os.environ.get("HYDRO_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "hydro_gb300", "autotune.json"))
+
+
+def signature(batch) -> str:
+    import torch
+
+    probs = batch.probs
+    p3 = [p for p in probs if p.ndim == 3]
+    cells = sum(p.ncell for p in p3)
+    ns = sorted(p.n[0] for p in p3)
+    prec = "fp32" if probs[0].precision == inputs.FP32 else "fp64"
+    hse = int(any(p.hse_subtract for p in p3))
+    mag = f"{cells:.2g}" if cells else "0"
+    span = f"{ns[0]}-{ns[-1]}" if ns else "none"
+    return f"{torch.cuda.get_device_name()}|{prec}|hse{hse}|n3d={len(p3)}|cells={mag}|n={span}"
+
+
+def _load_cache() -> Dict[str, dict]:
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(c: Dict[str, dict]):
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(c, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def time_steps(batch, steps: int) -> float:
+    """Milliseconds per step of the batch on its stream (CUDA events)."""
+    import torch
+
+    s = batch.stream
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    batch.step(steps)
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def tune_batch(batch, steps: int = 4, zchunks: Iterable[int] = DEFAULT_ZCHUNKS,
+               variants: Optional[Iterable[int]] = None, use_cache: bool = True) -> dict:
+    """Configure `batch` with the fastest (tile variant, z-chunk) and return
+    the choice with the timing table."""
+    from . import hydro
+
+    key = signature(batch)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        ch = cache[key]
+        batch.configure(ch["variant"], ch["zchunk"])
+        return dict(ch, cached=True)
+    shapes = hydro.batch_variants()
+    variants = list(range(len(shapes))) if variants is None else list(variants)
+    table = []
+    best = None
+    for v in variants:
+        for z in zchunks:
+            batch.configure(v, z)
+            batch.step(2)                        # first launch of this kernel, warm caches
+            ms = time_steps(batch, steps)
+            table.append({"variant": v, "tile": list(shapes[v]), "zchunk": z, "ms_per_step": ms})
+            if best is None or ms < best["ms_per_step"]:
+                best = table[-1]
+    batch.configure(best["variant"], best["zchunk"])
+    choice = {"variant": best["variant"], "tile": best["tile"], "zchunk": best["zchunk"],
+              "ms_per_step": best["ms_per_step"], "table": table}
+    if use_cache:
+        cache[key] = choice
+        _store_cache(cache)
+    return dict(choice, cached=False)

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(AUX_THREADS) signal_kernel(const AuxArgs a)
     sa.partial = a.partial;
     sa.cfl = a.cfl;
     sa.t_end = 0.0;
-    finish_step<AUX_THREADS>(m, bad_cta, sa, gridDim.x, 0.0, false, &s_last);
+    finish_step<AUX_THREADS>(m, bad_cta, sa, gridDim.x, blockIdx.x, 0.0, false, &s_last);
 }
 
 // Deterministic FP64 totals: CTA b sums cells c = b*blockDim + t + j*stride

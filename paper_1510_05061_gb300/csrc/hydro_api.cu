@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -158,6 +159,7 @@ StepArgs step_args(const hydro_sim *s, double t_end)
     a.gamma = s->prob.gamma;
     a.cfl = s->prob.cfl;
     a.t_end = t_end;
+    a.step_end = LLONG_MAX;
     a.ctrl = s->ctrl;
     a.partial = s->partial;
     a.bgT = nullptr;

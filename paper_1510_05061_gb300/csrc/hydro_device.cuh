@@ -290,9 +290,11 @@ __device__ __forceinline__ double block_max(double v, double *red)
     return v;
 }
 
-// Last-CTA finalisation of a step's time control.  Every CTA calls it once
-// with its max signal speed (valid in thread 0) and whether any of its cells
-// failed the admissibility check, after storing its part of the new state.
+// Last-CTA finalisation of a step's time control.  Each of the nblocks
+// contributions (CTAs, or work items of one instance) calls it once with its
+// max signal speed (valid in thread 0), whether any of its cells failed the
+// admissibility check, and its slot `part` in a.partial, after storing its
+// part of the new state.
 // The CTA that arrives last takes the grid maximum (max is exact, so arrival
 // order does not matter), commits the error bits, sets the next dt in FP64
 // and advances time.  advance = false only recomputes dt (initialisation).
@@ -300,11 +302,12 @@ __device__ __forceinline__ double block_max(double v, double *red)
 // it does so after all CTAs have read them.
 template <int NT>
 __device__ __forceinline__ void finish_step(double smax_cta, bool bad_cta, const StepArgs &a,
-                                            int nblocks, double dt_used, bool advance, int *s_last)
+                                            int nblocks, int part, double dt_used, bool advance,
+                                            int *s_last)
 {
     if (threadIdx.x == 0) {
         if (bad_cta) atomicOr(&a.ctrl->err_new, 1);
-        a.partial[blockIdx.x + (size_t)blockIdx.y * gridDim.x] = smax_cta;
+        a.partial[part] = smax_cta;
         __threadfence();
         const unsigned prev = atomicAdd(&a.ctrl->counter, 1u);
         *s_last = (prev == (unsigned)(nblocks - 1));

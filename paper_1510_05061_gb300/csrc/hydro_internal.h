@@ -50,11 +50,27 @@ struct StepArgs {
     double gamma, cfl;
     double grav[3];
     double t_end;       // clamp target (+inf for a free step)
+    long long step_end; // no further steps once ctrl->step reaches it
     Ctrl *ctrl;
     double *partial;    // per-CTA max signal speed
     const void *bgT;    // hse tables in the step's precision (nullptr in plain mode)
     int zchunk;         // planes per CTA (3D)
     int tiles_x;        // tiles along x
+};
+
+// One item of a batched step's work list: a tile and z-chunk of one instance.
+struct BatchItem {
+    int inst;    // instance index
+    int tile;    // tile within the instance's x-y tiling
+    int chunk;   // z-chunk (0 in 2D)
+    int local;   // index of this item among the instance's items (its partial slot)
+};
+
+// Per-instance launch arguments for both ping-pong parities.
+struct BatchInst {
+    StepArgs a[2];
+    int nitems;  // items of this instance in the work list
+    int pad[3];
 };
 
 // Workspace layout (offsets in bytes from the workspace base).

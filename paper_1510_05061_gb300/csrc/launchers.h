@@ -15,6 +15,21 @@ constexpr int STEP3D_TY = 8;
 constexpr int STEP2D_TX = 32;
 constexpr int STEP2D_TY = 8;
 
+// Tile shapes of the batched 3D step (chosen per batch by the autotuner).
+struct TileShape { int tx, ty; };
+constexpr int BATCH3D_VARIANTS = 3;
+constexpr TileShape BATCH3D_SHAPES[BATCH3D_VARIANTS] = {{32, 8}, {32, 4}, {16, 16}};
+constexpr int BATCH2D_TX = 32, BATCH2D_TY = 8;
+
+// Persistent batched steps over a device work list; `grid` CTAs walk the
+// items.  *_max_grid: resident CTAs on the current device (SMs x occupancy).
+cudaError_t launch_batch3d(int variant, bool fp32, bool hse, const BatchInst *insts,
+                           const BatchItem *items, int nitems, int parity, int grid, cudaStream_t s);
+cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, const BatchItem *items, int nitems,
+                           int parity, int grid, cudaStream_t s);
+int batch3d_max_grid(int variant, bool fp32, bool hse);
+int batch2d_max_grid(bool fp32);
+
 cudaError_t launch_step3d_f64(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
 cudaError_t launch_step3d_f32(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
 cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32);

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "hydro_device.cuh"
+#include "step3d.cuh"   // BatchItem, BatchInst
 
 namespace hydro {
 
@@ -28,41 +29,41 @@ struct Step2DSmem {
 };
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
+__device__ __forceinline__ void step2d_copy(const StepArgs &a, int tile)
+{
+    constexpr int NV = 4;
+    const int nx = a.n[0], ny = a.n[1];
+    const int gx = (tile % a.tiles_x) * TX + threadIdx.x % TX;
+    const int gy = (tile / a.tiles_x) * TY + threadIdx.x / TX;
+    if (gx < nx && gy < ny)
+        for (int q = 0; q < NV; ++q) {
+            const size_t c = (size_t)q * a.vstride + (size_t)gy * nx + gx;
+            static_cast<T *>(a.Unew)[c] = static_cast<const T *>(a.U)[c];
+        }
+}
+
+// One CTA's share of a 2D step: tile `tile` (row-major over tiles_x).
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double dtd,
+                                            unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 2, NV = 4, NT = TX * TY;
     using S = Step2DSmem<T, TX, TY>;
     constexpr int HX = S::HX, HY = S::HY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *prim = reinterpret_cast<T *>(smem_raw);
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
     T *fxs = wyh + S::wy, *fys = fxs + S::fx;
-    __shared__ double red[32];
-    __shared__ int s_last;
 
     const int nx = a.n[0], ny = a.n[1];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = (blockIdx.x % a.tiles_x) * TX;
-    const int y0 = (blockIdx.x / a.tiles_x) * TY;
-    const int nblocks = gridDim.x * gridDim.y;
+    const int x0 = (tile % a.tiles_x) * TX;
+    const int y0 = (tile / a.tiles_x) * TY;
     const T *__restrict__ U = static_cast<const T *>(a.U);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
     const long long vs = a.vstride;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
-
-    const double t_now = a.ctrl->t;
-    const double dt_cfl = a.ctrl->dt_next;
-    if (t_now >= a.t_end || a.ctrl->err != 0) {
-        if (own)
-            for (int q = 0; q < NV; ++q) {
-                const size_t c = (size_t)q * vs + (size_t)gy * nx + gx;
-                Un[c] = U[c];
-            }
-        return;
-    }
-    const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
     const T gam = T(a.gamma);
     const T igm1 = T(1.0 / (a.gamma - 1.0));
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     __syncthreads();
 
     // ---- update, admissibility, CFL signal speed
-    T smax = T(0);
-    bool bad = false;
+    smax = T(0);
+    bad = false;
     if (own) {
         const size_t c = (size_t)gy * nx + gx;
         T u[NV], du[NV];
@@ -211,9 +212,65 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
         if (!(u[0] > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
         else smax = s;
     }
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
+{
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int s_last;
+    const double t_now = a.ctrl->t;
+    const double dt_cfl = a.ctrl->dt_next;
+    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
+        step2d_copy<T, TX, TY>(a, blockIdx.x);
+        return;
+    }
+    const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
+    T smax;
+    bool bad;
+    step2d_body<T, TX, TY>(a, blockIdx.x, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     const double m = block_max<NT>(double(smax), red);
-    finish_step<NT>(m, bad_cta, a, nblocks, dtd, true, &s_last);
+    finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd,
+                    true, &s_last);
+}
+
+// Persistent batched 2D step over a work list of (instance, tile) items; the
+// BatchItem/BatchInst layout is shared with the 3D batch (chunk unused).
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+step2d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
+                    int nitems, int parity)
+{
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int s_last;
+    __shared__ StepArgs sa;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        if (threadIdx.x < (int)(sizeof(StepArgs) / sizeof(int))) {
+            reinterpret_cast<int *>(&sa)[threadIdx.x] =
+                reinterpret_cast<const int *>(&insts[w.inst].a[parity])[threadIdx.x];
+        }
+        __syncthreads();
+        const double t_now = sa.ctrl->t;
+        const double dt_cfl = sa.ctrl->dt_next;
+        if (t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end) {
+            step2d_copy<T, TX, TY>(sa, w.tile);
+        } else {
+            const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
+            T smax;
+            bool bad;
+            step2d_body<T, TX, TY>(sa, w.tile, dtd, smem_raw, smax, bad);
+            const bool bad_cta = __syncthreads_or(bad) != 0;
+            const double m = block_max<NT>(double(smax), red);
+            finish_step<NT>(m, bad_cta, sa, insts[w.inst].nitems, w.local, dtd, true, &s_last);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace hydro

@@ -36,8 +36,33 @@ struct Step3DSmem {
     static constexpr size_t bytes = elems * sizeof(T);
 };
 
+// Frozen step (time already at t_end, or the handle in its error state):
+// the tile's cells are carried over unchanged.
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chunk)
+{
+    constexpr int NV = 5;
+    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int gx = (tile % a.tiles_x) * TX + tx, gy = (tile / a.tiles_x) * TY + ty;
+    const int z0 = chunk * a.zchunk, z1 = min(z0 + a.zchunk, nz);
+    const T *U = static_cast<const T *>(a.U);
+    T *Un = static_cast<T *>(a.Unew);
+    if (gx < nx && gy < ny)
+        for (int k = z0; k < z1; ++k)
+            for (int q = 0; q < NV; ++q) {
+                const size_t c = (size_t)q * a.vstride + (size_t)k * a.plane + (size_t)gy * nx + gx;
+                Un[c] = U[c];
+            }
+}
+
+// One CTA's share of a step: tile `tile` (row-major over tiles_x) of the x-y
+// plane, z planes [chunk*zchunk, min((chunk+1)*zchunk, nz)), time step dtd.
+// On return smax/bad hold this thread's max CFL signal speed and whether one
+// of its new cells failed the admissibility check.
 template <typename T, bool HSE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1) step3d_kernel(const StepArgs a)
+__device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chunk, double dtd,
+                                            unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
     // FP32 keeps the next plane's loads in flight; FP64 is bound by its
@@ -45,40 +70,20 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1) step3d_kernel
     constexpr bool PREFETCH = sizeof(T) == 4;
     using S = Step3DSmem<T, HSE, TX, TY>;
     constexpr int HX = S::HX, HY = S::HY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *prim = reinterpret_cast<T *>(smem_raw);
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
     T *fxs = wyh + S::wy, *fys = fxs + S::fx;
-    __shared__ double red[32];
-    __shared__ int s_last;
 
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = (blockIdx.x % a.tiles_x) * TX;
-    const int y0 = (blockIdx.x / a.tiles_x) * TY;
-    const int z0 = blockIdx.y * a.zchunk;
+    const int x0 = (tile % a.tiles_x) * TX;
+    const int y0 = (tile / a.tiles_x) * TY;
+    const int z0 = chunk * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
-    const int nblocks = gridDim.x * gridDim.y;
     const T *__restrict__ U = static_cast<const T *>(a.U);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
     const long long vs = a.vstride;
-
-    // ---- time control: dt from the device block, clamped to t_end
-    const double t_now = a.ctrl->t;
-    const double dt_cfl = a.ctrl->dt_next;
-    if (t_now >= a.t_end || a.ctrl->err != 0) {
-        // finished or failed: carry the state over unchanged
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx < nx && gy < ny)
-            for (int k = z0; k < z1; ++k)
-                for (int q = 0; q < NV; ++q) {
-                    const size_t c = (size_t)q * vs + (size_t)k * a.plane + (size_t)gy * nx + gx;
-                    Un[c] = U[c];
-                }
-        return;
-    }
-    const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
     const T gam = T(a.gamma);
     const T igm1 = T(1.0 / (a.gamma - 1.0));
@@ -168,8 +173,8 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1) step3d_kernel
     T msrc_prev = T(0);
 #pragma unroll
     for (int q = 0; q < NV; ++q) { ztop_prev[q] = T(0); fz_prev[q] = T(0); div_prev[q] = T(0); }
-    T smax = T(0);
-    bool bad = false;
+    smax = T(0);
+    bad = false;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
 
@@ -346,9 +351,69 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1) step3d_kernel
         for (int q = 0; q < NV; ++q) { ztop_prev[q] = ztop[q]; fz_prev[q] = fz[q]; }
     }
 
+}
+
+template <typename T, bool HSE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1) step3d_kernel(const StepArgs a)
+{
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int s_last;
+    const int tile = blockIdx.x, chunk = blockIdx.y;
+    // time control: dt from the device block, clamped to t_end
+    const double t_now = a.ctrl->t;
+    const double dt_cfl = a.ctrl->dt_next;
+    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
+        step3d_copy<T, TX, TY>(a, tile, chunk);
+        return;
+    }
+    const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
+    T smax;
+    bool bad;
+    step3d_body<T, HSE, TX, TY>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     const double m = block_max<NT>(double(smax), red);
-    finish_step<NT>(m, bad_cta, a, nblocks, dtd, true, &s_last);
+    finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd,
+                    true, &s_last);
+}
+
+// Persistent batched step: a fixed grid walks the work list of all
+// instances (item it goes to CTA it mod gridDim.x).  Each instance keeps its
+// own time-control block; the CTA that completes the instance's last item
+// sets that instance's next dt (per-instance CFL).
+template <typename T, bool HSE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? 2 : 1)
+step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
+                    int nitems, int parity)
+{
+    constexpr int NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int s_last;
+    __shared__ StepArgs sa;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        if (threadIdx.x < (int)(sizeof(StepArgs) / sizeof(int))) {
+            reinterpret_cast<int *>(&sa)[threadIdx.x] =
+                reinterpret_cast<const int *>(&insts[w.inst].a[parity])[threadIdx.x];
+        }
+        __syncthreads();
+        const double t_now = sa.ctrl->t;
+        const double dt_cfl = sa.ctrl->dt_next;
+        if (t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end) {
+            step3d_copy<T, TX, TY>(sa, w.tile, w.chunk);
+        } else {
+            const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
+            T smax;
+            bool bad;
+            step3d_body<T, HSE, TX, TY>(sa, w.tile, w.chunk, dtd, smem_raw, smax, bad);
+            const bool bad_cta = __syncthreads_or(bad) != 0;
+            const double m = block_max<NT>(double(smax), red);
+            finish_step<NT>(m, bad_cta, sa, insts[w.inst].nitems, w.local, dtd, true, &s_last);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace hydro

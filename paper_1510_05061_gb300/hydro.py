@@ -45,7 +45,12 @@ EXPORTS = (
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
     "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk",
     "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
-    "hydro_selftest_math",
+    "hydro_selftest_math", "hydro_batch_workspace_bytes", "hydro_batch_init",
+    "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
+    "hydro_batch_create", "hydro_batch_add", "hydro_batch_remove", "hydro_batch_set_graph",
+    "hydro_batch_configure", "hydro_batch_variant_shape", "hydro_batch_step", "hydro_batch_reduce",
+    "hydro_batch_get_fields", "hydro_batch_get_state", "hydro_batch_current", "hydro_batch_launch_count", "hydro_batch_items",
+    "hydro_batch_destroy",
 )
 
 
@@ -111,6 +116,45 @@ def load(path: str = LIB_PATH):
     L.hydro_strerror.argtypes = [C.c_int]
     L.hydro_selftest_math.restype = C.c_int
     L.hydro_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_long, vp]
+    PP = C.POINTER(C.c_void_p)
+    L.hydro_batch_workspace_bytes.restype = C.c_size_t
+    L.hydro_batch_workspace_bytes.argtypes = [P, C.c_int]
+    L.hydro_batch_init.restype = C.c_int
+    L.hydro_batch_init.argtypes = [P, C.c_int, PP, PP, vp, PP, PP, vp, C.POINTER(vp)]
+    L.hydro_instance_work_bytes.restype = C.c_size_t
+    L.hydro_instance_work_bytes.argtypes = [P]
+    L.hydro_problem_max_items.restype = C.c_long
+    L.hydro_problem_max_items.argtypes = [P]
+    L.hydro_batch_create_bytes.restype = C.c_size_t
+    L.hydro_batch_create_bytes.argtypes = [C.c_int, C.c_long, C.c_long]
+    L.hydro_batch_create.restype = C.c_int
+    L.hydro_batch_create.argtypes = [C.c_int, C.c_long, C.c_long, C.c_int, vp, vp, C.POINTER(vp)]
+    L.hydro_batch_add.restype = C.c_int
+    L.hydro_batch_add.argtypes = [vp, P, vp, vp, vp, D, D, C.c_long, C.POINTER(C.c_int)]
+    L.hydro_batch_remove.restype = C.c_int
+    L.hydro_batch_remove.argtypes = [vp, C.c_int]
+    L.hydro_batch_set_graph.restype = C.c_int
+    L.hydro_batch_set_graph.argtypes = [vp, C.c_int]
+    L.hydro_batch_configure.restype = C.c_int
+    L.hydro_batch_configure.argtypes = [vp, C.c_int, C.c_int]
+    L.hydro_batch_variant_shape.restype = C.c_int
+    L.hydro_batch_variant_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.hydro_batch_step.restype = C.c_int
+    L.hydro_batch_step.argtypes = [vp, C.c_long]
+    L.hydro_batch_reduce.restype = C.c_int
+    L.hydro_batch_reduce.argtypes = [vp, C.c_int, C.c_int, D]
+    L.hydro_batch_get_fields.restype = C.c_int
+    L.hydro_batch_get_fields.argtypes = [vp, C.c_int, C.c_int, D]
+    L.hydro_batch_get_state.restype = C.c_int
+    L.hydro_batch_get_state.argtypes = [vp, C.c_int, vp]
+    L.hydro_batch_current.restype = vp
+    L.hydro_batch_current.argtypes = [vp, C.c_int]
+    L.hydro_batch_launch_count.restype = C.c_long
+    L.hydro_batch_launch_count.argtypes = [vp]
+    L.hydro_batch_items.restype = C.c_int
+    L.hydro_batch_items.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
+    L.hydro_batch_destroy.restype = C.c_int
+    L.hydro_batch_destroy.argtypes = [vp]
     L.hydro_totals_noalloc.restype = C.c_int
     L.hydro_totals_noalloc.argtypes = [P, vp, D, vp, D]
     _lib = L
@@ -353,6 +397,125 @@ class Simulation:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             hydro_destroy(self.h)
+            self.h = None
+        self._bufs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- batches
+
+def hydro_batch_variant_shape(v: int):
+    tx, ty = C.c_int(), C.c_int()
+    _check(load().hydro_batch_variant_shape(int(v), C.byref(tx), C.byref(ty)), "hydro_batch_variant_shape")
+    return tx.value, ty.value
+
+
+def batch_variants():
+    """Tile shapes (TX, TY) the batched 3D step can use, by variant index."""
+    out = []
+    v = 0
+    while load().hydro_batch_variant_shape(v, C.byref(C.c_int()), C.byref(C.c_int())) == HYDRO_OK:
+        out.append(hydro_batch_variant_shape(v))
+        v += 1
+    return out
+
+
+class Batch:
+    """Independent instances (list of (Problem, W0)) advanced together by
+    the batched persistent step.  Runs on its own torch CUDA stream so that
+    the step can be captured into a CUDA graph."""
+
+    def __init__(self, items, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhydro needs a CUDA device")
+        self.probs = [p for p, _ in items]
+        n = len(items)
+        arr = (hydro_problem * n)(*[make_problem(p) for p in self.probs])
+        self._arr = arr
+        wb = load().hydro_batch_workspace_bytes(arr, n)
+        if wb == 0:
+            raise HydroError(HYDRO_ERR_INVALID_ARG, "batch problems")
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self._bufs = []
+        ua, ub = [], []
+        for p in self.probs:
+            sb = hydro_state_bytes(make_problem(p))
+            for lst in (ua, ub):
+                t = torch.empty(sb + 256, dtype=torch.uint8, device=dev)
+                self._bufs.append(t)
+                lst.append((t.data_ptr() + 255) // 256 * 256)
+        wt = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
+        self._bufs.append(wt)
+        work = (wt.data_ptr() + 255) // 256 * 256
+        self._W = [np.ascontiguousarray(W, dtype=np.float64) for _, W in items]
+        self._bg = [background_tables(p) for p in self.probs]
+        VP = C.c_void_p * n
+        Wp = VP(*[w.ctypes.data for w in self._W])
+        Bp = VP(*[(b.ctypes.data if b is not None else None) for b in self._bg])
+        torch.cuda.synchronize()
+        h = C.c_void_p()
+        rc = load().hydro_batch_init(arr, n, VP(*ua), VP(*ub), C.c_void_p(work), Wp, Bp,
+                                     C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if rc != HYDRO_OK and h.value:
+            load().hydro_batch_destroy(h)
+        _check(rc, "hydro_batch_init")
+        self.h = h
+        self.count = n
+
+    def configure(self, variant: int, zchunk: int = 0):
+        _check(load().hydro_batch_configure(self.h, int(variant), int(zchunk)), "hydro_batch_configure")
+
+    def step(self, n: int = 1):
+        _check(load().hydro_batch_step(self.h, int(n)), "hydro_batch_step")
+
+    def reduce(self, i: int, what: int) -> np.ndarray:
+        out = np.zeros(max(self.probs[i].nvar, 1), dtype=np.float64)
+        _check(load().hydro_batch_reduce(self.h, int(i), int(what), _dptr(out)), "hydro_batch_reduce")
+        return out
+
+    def t(self, i: int) -> float:
+        return float(self.reduce(i, HYDRO_RED_TIME)[0])
+
+    def nstep(self, i: int) -> int:
+        return int(self.reduce(i, HYDRO_RED_STEP)[0])
+
+    def totals(self, i: int) -> np.ndarray:
+        return self.reduce(i, HYDRO_RED_TOTALS)
+
+    def conserved(self, i: int) -> np.ndarray:
+        out = np.empty(self.probs[i].shape, dtype=np.float64)
+        _check(load().hydro_batch_get_fields(self.h, int(i), 0, _dptr(out)), "hydro_batch_get_fields")
+        return out
+
+    def get_state(self, i: int) -> np.ndarray:
+        p = self.probs[i]
+        out = np.empty(p.shape, dtype=np.float32 if p.precision == inputs.FP32 else np.float64)
+        _check(load().hydro_batch_get_state(self.h, int(i), C.c_void_p(out.ctypes.data)),
+               "hydro_batch_get_state")
+        return out
+
+    def launches(self) -> int:
+        return load().hydro_batch_launch_count(self.h)
+
+    def items(self):
+        v = [C.c_int() for _ in range(4)]
+        _check(load().hydro_batch_items(self.h, *[C.byref(x) for x in v]), "hydro_batch_items")
+        return tuple(x.value for x in v)
+
+    def cells(self) -> int:
+        return sum(p.ncell for p in self.probs)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().hydro_batch_destroy(self.h)
             self.h = None
         self._bufs = []
 

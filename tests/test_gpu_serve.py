@@ -1,0 +1,90 @@
+"""Continuous-batching server: requests join and leave the batch between
+steps, admission is bounded by slots and an HBM budget, and every served
+result equals the same solve run alone (bit for bit: the per-cell arithmetic
+does not depend on which other solves share the launch)."""
+
+import numpy as np
+import pytest
+
+from paper_1510_05061_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_05061_gb300 import build, hydro, serve
+
+    build.build()
+    hydro.load()
+    return torch, hydro, serve
+
+
+def small_requests(serve):
+    specs = [("kh2d", 48, 12), ("rt3d", 16, 9), ("kh2d", 37, 15), ("rt3d", 24, 6),
+             ("kh2d", 64, 7), ("rt3d", 20, 11), ("kh2d", 33, 5)]
+    reqs = []
+    for i, (fam, n, steps) in enumerate(specs):
+        r = serve.Request(id=i, arrival=0.002 * i, family=fam, n=n, steps=steps, seed=151005063 + i)
+        reqs.append(serve.make_payload(r))
+    return reqs
+
+
+def solo_state(hydro, req):
+    sim = hydro.Simulation(req.prob, req.W)
+    sim.run_steps(req.steps)
+    out = sim.get_state()
+    sim.close()
+    return out
+
+
+def test_served_results_equal_solo_and_budget_binds(env):
+    torch, hydro, serve = env
+    reqs = small_requests(serve)
+    probe = serve.Server(budget_bytes=1e12, max_active=8, max_items3d=200000, max_items2d=20000)
+    sizes = [probe.request_bytes(r) for r in reqs]
+    probe.close()
+    budget = 2.2 * max(sizes)            # at most a few solves fit at once
+    srv = serve.Server(budget_bytes=budget, max_active=8, max_items3d=200000, max_items2d=20000)
+    peak = {"n": 0, "mixed": False}
+    orig_tick = srv.tick
+
+    def tick():
+        peak["n"] = max(peak["n"], len(srv.active))
+        fams = {r.family for r in srv.active.values()}
+        peak["mixed"] |= len(fams) == 2
+        assert srv.used <= budget
+        return orig_tick()
+
+    srv.tick = tick
+    stats = srv.run(reqs, keep_results=lambda r: True)
+    srv.close()
+    assert stats["requests"] == len(reqs)
+    assert 2 <= peak["n"] < len(reqs)     # solves overlapped, and the budget held some back
+    assert peak["mixed"]                  # 2D and 3D solves shared ticks
+    assert stats["p99_latency_s"] >= stats["p50_latency_s"] > 0
+    for r in reqs:
+        assert np.array_equal(r.result, solo_state(hydro, r)), r.id
+
+
+def test_slot_limit_and_reuse(env):
+    torch, hydro, serve = env
+    reqs = small_requests(serve)[:5]
+    srv = serve.Server(budget_bytes=1e12, max_active=2, max_items3d=200000, max_items2d=20000)
+    seen = []
+    orig = srv.tick
+
+    def tick():
+        seen.append(len(srv.active))
+        return orig()
+
+    srv.tick = tick
+    stats = srv.run(reqs, keep_results=lambda r: True)
+    srv.close()
+    assert max(seen) <= 2 and stats["requests"] == 5
+    for r in reqs:
+        assert np.array_equal(r.result, solo_state(hydro, r)), r.id
