@@ -58,6 +58,12 @@ CONFIGS = {
                        desc="3D Rayleigh-Taylor 512^3 FP32 bulk, FP64 dt/totals/background subtraction"),
     "rt256-fp32": dict(n=256, precision=inputs.FP32, hse=1,
                        desc="3D Rayleigh-Taylor 256^3 FP32 bulk with hydrostatic-background subtraction"),
+    "served": dict(served=True, rate=50.0,
+                   desc="served workload: Poisson arrivals (50/s, seed 151005063), 50/50 2D KH n in [64, 2048] "
+                        "and 3D RT n in [32, 256] (log-uniform), 100-1000 steps each, FP32 with FP64 "
+                        "reductions, 150 GB HBM budget, continuous batching"),
+    "served-saturation": dict(served=True, rate=500.0,
+                              desc="served workload as above with arrivals 10x faster (saturation run)"),
     "kh-batch": dict(batch=True, count=64, precision=inputs.FP32,
                      desc="64 independent 3D periodic Kelvin-Helmholtz boxes, n log-uniform in [32, 192] "
                           "(seed 151005062), FP32; one persistent launch per step, autotuned tiles"),
@@ -174,8 +180,8 @@ def max_over_ranks(world, x: float) -> float:
 
 def build_workload(cfg):
     c = CONFIGS[cfg]
-    if c.get("batch"):
-        raise ValueError("batch configs have no single workload")
+    if c.get("batch") or c.get("served"):
+        raise ValueError("batch and served configs have no single workload")
     prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
     return prob, W, c
 
@@ -323,10 +329,59 @@ def run_gpu_batch(args):
     return 0
 
 
+# ------------------------------------------------------------- served arm
+def run_served(args):
+    import torch
+
+    from paper_1510_05061_gb300 import build as hbuild
+    from paper_1510_05061_gb300 import hydro, serve
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hydro.load()
+    c = CONFIGS[args.config]
+    t0 = time.perf_counter()
+    reqs = serve.requests_from_inputs(count=args.requests, rate=c["rate"])
+    prep_s = time.perf_counter() - t0
+    srv = serve.Server(budget_bytes=args.budget_gb * 1e9, max_active=args.max_active)
+    barrier(world)
+    with ClockSampler(local) as clk:
+        stats = srv.run(reqs)
+    srv.close()
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    busy_gbs = stats["busy_hbm_gbs"] or 0.0
+    value = stats["zone_updates_per_s"] * world
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": stats["ticks"], "warmup": 0, "ms_per_step": 1e3 * stats["busy_s"] / max(stats["ticks"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": c["desc"], "requests": stats["requests"], "rate_per_s": c["rate"],
+                       "budget_gb": args.budget_gb, "max_active": args.max_active,
+                       "payload_prep_s": prep_s, "step": "one tick = one batched step of every active solve",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "latency": {"p50_s": stats["p50_latency_s"], "p99_s": stats["p99_latency_s"],
+                        "makespan_s": stats["makespan_s"]},
+            "roofline": {"bound": "hbm", "achieved": busy_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": busy_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "step3d_batch_kernel<float> + step2d_batch_kernel<float>",
+                         "note": "algorithmic bytes over busy (tick) time"},
+            "busy_zone_updates_per_s": stats["busy_zone_updates_per_s"],
+            "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------- GPU arm
 def run_gpu(args):
     if CONFIGS[args.config].get("batch"):
         return run_gpu_batch(args)
+    if CONFIGS[args.config].get("served"):
+        return run_served(args)
     import torch
 
     from paper_1510_05061_gb300 import build as hbuild
@@ -494,6 +549,9 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the step kernel from an ncu capture")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--requests", type=int, default=200, help="served configs: number of requests")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served configs: HBM budget")
+    ap.add_argument("--max-active", type=int, default=64, help="served configs: concurrent solves")
     ap.add_argument("--precision-report", action="store_true",
                     help="FP32 vs FP64 Rayleigh-Taylor density error at t_end (no JSON bench line)")
     ap.add_argument("--precision-n", type=int, default=512)

@@ -251,11 +251,16 @@ def rayleigh_taylor(n: int = 256, seed: int = 151005061, nz: Optional[int] = Non
     if perturb:
         ks, amp, phase = rt_modes(seed)
         norm = math.sqrt(0.5 * float(np.sum(amp * amp)))
-        plane = np.zeros((n, n), dtype=np.float64)
-        twopi = 2.0 * math.pi
+        # sum_k a_k cos(2 pi (kx x + ky y) + phi_k) = Re(Y^T A X) with
+        # A[ky, kx] = a_k exp(i phi_k), X[kx, x] = exp(2 pi i kx x),
+        # Y[ky, y] = exp(2 pi i ky y): a small complex matrix product
+        kmax = int(np.abs(ks).max())
+        A = np.zeros((kmax + 1, 2 * kmax + 1), dtype=np.complex128)
         for (kx, ky), a, ph in zip(ks, amp, phase):
-            plane += a * np.cos(twopi * (kx * x[None, :] + ky * y[:, None]) + ph)
-        plane /= norm
+            A[int(ky), int(kx) + kmax] += a * np.exp(1j * ph)
+        X = np.exp(2j * math.pi * np.outer(np.arange(-kmax, kmax + 1), x))
+        Y = np.exp(2j * math.pi * np.outer(np.arange(0, kmax + 1), y))
+        plane = np.real(Y.T @ A @ X) / norm
         env = amplitude * np.exp(-((z - RT_Z_INTERFACE) / 0.1) ** 2)
         W[3] = env[:, None, None] * plane[None, :, :]
     return prob, W

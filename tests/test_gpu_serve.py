@@ -25,11 +25,12 @@ def env():
 
 
 def small_requests(serve):
+    # all arrive at once, so that slots and the memory budget decide admission
     specs = [("kh2d", 48, 12), ("rt3d", 16, 9), ("kh2d", 37, 15), ("rt3d", 24, 6),
              ("kh2d", 64, 7), ("rt3d", 20, 11), ("kh2d", 33, 5)]
     reqs = []
     for i, (fam, n, steps) in enumerate(specs):
-        r = serve.Request(id=i, arrival=0.002 * i, family=fam, n=n, steps=steps, seed=151005063 + i)
+        r = serve.Request(id=i, arrival=0.0, family=fam, n=n, steps=steps, seed=151005063 + i)
         reqs.append(serve.make_payload(r))
     return reqs
 
