@@ -58,6 +58,10 @@ CONFIGS = {
                        desc="3D Rayleigh-Taylor 512^3 FP32 bulk, FP64 dt/totals/background subtraction"),
     "rt256-fp32": dict(n=256, precision=inputs.FP32, hse=1,
                        desc="3D Rayleigh-Taylor 256^3 FP32 bulk with hydrostatic-background subtraction"),
+    "sod128": dict(kind="sod", n=128, precision=inputs.FP64, hse=0,
+                   desc="2D Sod shock tube 128^2 FP64 (latency-bound: 0.5 MB state fits in L2)"),
+    "kh2d-2048-fp32": dict(kind="kh2d", n=2048, precision=inputs.FP32, hse=0,
+                           desc="2D Kelvin-Helmholtz 2048^2 FP32 (largest 2D served size)"),
     "served": dict(served=True, rate=50.0,
                    desc="served workload: Poisson arrivals (50/s, seed 151005063), 50/50 2D KH n in [64, 2048] "
                         "and 3D RT n in [32, 256] (log-uniform), 100-1000 steps each, FP32 with FP64 "
@@ -182,7 +186,13 @@ def build_workload(cfg):
     c = CONFIGS[cfg]
     if c.get("batch") or c.get("served"):
         raise ValueError("batch and served configs have no single workload")
-    prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
+    kind = c.get("kind", "rt")
+    if kind == "sod":
+        prob, W = inputs.sod(c["n"], precision=c["precision"])
+    elif kind == "kh2d":
+        prob, W = inputs.kelvin_helmholtz(c["n"], ndim=2, U=1.0, ratio=2.0, precision=c["precision"])
+    else:
+        prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
     return prob, W, c
 
 
@@ -194,8 +204,8 @@ def oracle_sample(seconds: float = 10.0, max_steps: int = 1000, cfg="rt256-fp64"
 
     oracle.build()
     prob, W, c = build_workload(cfg)
-    desc = f"{c['n']}^3 full grid"
-    if nz_slab is not None:
+    desc = f"full {'x'.join(str(v) for v in prob.n[:prob.ndim])} grid"
+    if nz_slab is not None and prob.ndim == 3 and prob.n[2] > nz_slab:
         # a slab of nz_slab planes around the interface, same x-y extent
         k0 = prob.n[2] // 2 - nz_slab // 2
         z_lo = prob.lo[2] + k0 * prob.dx()[2]
@@ -225,19 +235,27 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = args.config
+    if CONFIGS[cfg].get("batch") or CONFIGS[cfg].get("served"):
+        cfg = "rt256-fp64"      # the oracle times a single solve; batches are sums of such solves
     prob, W, c = build_workload(cfg)
     import oracle
 
     oracle.build()
     nz_slab = 16
-    k0 = prob.n[2] // 2 - nz_slab // 2
-    sprob = prob.replace(n=(prob.n[0], prob.n[1], nz_slab),
-                         lo=(0.0, 0.0, prob.lo[2] + k0 * prob.dx()[2]),
-                         hi=(1.0, 1.0, prob.lo[2] + (k0 + nz_slab) * prob.dx()[2]))
-    if prob.hse_subtract:
-        sprob = sprob.replace(bg_rho_c=prob.bg_rho_c[k0:k0 + nz_slab + 4], bg_p_c=prob.bg_p_c[k0:k0 + nz_slab + 4],
-                              bg_rho_f=prob.bg_rho_f[k0:k0 + nz_slab + 5], bg_p_f=prob.bg_p_f[k0:k0 + nz_slab + 5])
-    Ws = np.ascontiguousarray(W[:, k0:k0 + nz_slab])
+    if prob.ndim == 3 and prob.n[2] > nz_slab:
+        k0 = prob.n[2] // 2 - nz_slab // 2
+        sprob = prob.replace(n=(prob.n[0], prob.n[1], nz_slab),
+                             lo=(0.0, 0.0, prob.lo[2] + k0 * prob.dx()[2]),
+                             hi=(1.0, 1.0, prob.lo[2] + (k0 + nz_slab) * prob.dx()[2]))
+        if prob.hse_subtract:
+            sprob = sprob.replace(bg_rho_c=prob.bg_rho_c[k0:k0 + nz_slab + 4], bg_p_c=prob.bg_p_c[k0:k0 + nz_slab + 4],
+                                  bg_rho_f=prob.bg_rho_f[k0:k0 + nz_slab + 5], bg_p_f=prob.bg_p_f[k0:k0 + nz_slab + 5])
+        Ws = np.ascontiguousarray(W[:, k0:k0 + nz_slab])
+        sample_desc = (f"{sprob.n[0]}x{sprob.n[1]}x{nz_slab} slab of the {c['n']}^3 initial state "
+                       f"around the interface; one FP64 oracle step per bench step")
+    else:
+        sprob, Ws = prob, W
+        sample_desc = f"the full {'x'.join(str(v) for v in prob.n[:prob.ndim])} grid; one oracle step per bench step"
     o = oracle.Oracle(sprob)
     U = o.state_from_prim(Ws)
     for _ in range(args.warmup):
@@ -248,8 +266,7 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = sprob.ncell * args.steps / el
     cores = o.L.orc_max_threads()
-    sample = (f"{sprob.n[0]}x{sprob.n[1]}x{nz_slab} slab of the {c['n']}^3 Rayleigh-Taylor initial state "
-              f"around the interface; one FP64 oracle step per bench step")
+    sample = sample_desc
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -455,23 +472,25 @@ def run_gpu(args):
     peaks, peak_kind = measured_peaks()
     bytes_per_zone = 2 * prob.nvar * itemsize
     zones_per_launch = N
+    flops_per_zone = FLOPS_PER_ZONE_3D if prob.ndim == 3 else FLOPS_PER_ZONE_2D
     achieved_gbs = bytes_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
     if prob.precision == inputs.FP64:
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak_tf = fp64_peak_tflops(sm_mhz)
-        ach_tf = FLOPS_PER_ZONE_3D * zones_per_launch / (kern_avg_ms * 1e-3) / 1e12
+        ach_tf = flops_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": ach_tf / peak_tf, "traffic": args.traffic,
                     "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
-                    "kernel": "step3d_kernel<double>",
+                    "kernel": "step3d_kernel<double>" if prob.ndim == 3 else "step2d_kernel<double>",
                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                             "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind}}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "traffic": args.traffic,
-                    "peak_kind": peak_kind, "kernel": "step3d_kernel<float>"}
+                    "peak_kind": peak_kind,
+                    "kernel": "step3d_kernel<float>" if prob.ndim == 3 else "step2d_kernel<float>"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -486,7 +505,8 @@ def run_gpu(args):
             "dtype": "f32" if itemsize == 4 else "f64", "data": "synthetic",
             "config": {"workload": c["desc"], "grid": list(prob.n), "precision": "fp32" if itemsize == 4 else "fp64",
                        "hse_subtract": prob.hse_subtract, "state_bytes": N * prob.nvar * itemsize,
-                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (N * prob.nvar * itemsize / 1e6),
+                       "l2": ("inputs larger than L2 (state %.0f MB > 129 MB)" if N * prob.nvar * itemsize > 129e6 else
+               "state %.1f MB fits in L2 (latency-bound configuration)") % (N * prob.nvar * itemsize / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "kernel_ms_avg": kern_avg_ms,
             "roofline": roofline,

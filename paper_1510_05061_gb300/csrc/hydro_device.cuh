@@ -68,6 +68,13 @@ __device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, 
 // an integer test of the bit pattern, which keeps it off the FP64 pipe.
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+// Sign tests for the HLLC fan branches: x >= 0 and x <= 0, by sign bit for
+// doubles (a signed zero may fall on either side; the flux is continuous
+// across both branch boundaries, so this only moves rounding).
+__device__ __forceinline__ bool nonnegative(double x) { return __double_as_longlong(x) >= 0; }
+__device__ __forceinline__ bool nonnegative(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool nonpositive(double x) { return __double_as_longlong(x) <= 0; }
+__device__ __forceinline__ bool nonpositive(float x) { return x <= 0.0f; }
 
 // MC limiter (van Leer 1977): full-cell slope sign(dr) min(2|dl|, 2|dr|,
 // |dl+dr|/2) when dl and dr have the same sign, else 0.
@@ -213,18 +220,18 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     const T sl = fmin(ul - cl, ur - cr);
     const T sr = fmax(ul + cl, ur + cr);
 
-    bool left, star;
-    T sstar = T(0);
-    if (T(0) <= sl) { left = true; star = false; }
-    else if (sr <= T(0)) { left = false; star = false; }
-    else {
-        // pressure difference from the perturbations: the background cancels
-        const T dpp = wr[NV - 1] - wl[NV - 1];
-        const T ml = rl * (sl - ul), mr = rr * (sr - ur);
-        sstar = div_t(dpp + ml * ul - mr * ur, ml - mr);
-        left = sstar >= T(0);
-        star = true;
-    }
+    // Branch-free: every face computes S* and the star correction and the
+    // branch of the HLLC fan is applied by selects.  The chosen branch's
+    // values are the same as with branches, and the straight-line code lets
+    // a thread's independent faces interleave.  S* and 1/(S_K - S*) are
+    // finite for positive densities and pressures (S_L < u_L, S_R > u_R).
+    const T dpp = wr[NV - 1] - wl[NV - 1];   // background cancels in the difference
+    const T ml = rl * (sl - ul), mr = rr * (sr - ur);
+    const T sstar = div_t(dpp + ml * ul - mr * ur, ml - mr);
+    const bool sup_l = nonnegative(sl);     // whole fan moves right: F_L
+    const bool sup_r = nonpositive(sr);     // whole fan moves left: F_R
+    const bool left = sup_l || (!sup_r && nonnegative(sstar));
+    const bool star = !sup_l && !sup_r;
     const T rk = left ? rl : rr;
     const T pk = left ? pl : pr;
     const T ppk = left ? wl[NV - 1] : wr[NV - 1];
@@ -246,21 +253,22 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     f[1 + D] += ppk;
     f[NV - 1] = uk * (Ek + pk);
 
-    if (star) {
-        // F*_K = F_K + S_K (U*_K - U_K)
-        const T skmu = sk - uk;
-        const T q = rcp_t(sk - sstar);
-        const T mk = rk * skmu;
-        const T fac = mk * q;
-        const T e_star = q * (skmu * Ek + (sstar - uk) * (mk * sstar + pk));
-        f[0] += sk * (fac - rk);
+    // F*_K = F_K + S_K (U*_K - U_K), applied only inside the fan
+    const T skmu = sk - uk;
+    const T q = rcp_t(sk - sstar);
+    const T mk = rk * skmu;
+    const T fac = mk * q;
+    const T e_star = q * (skmu * Ek + (sstar - uk) * (mk * sstar + pk));
+    const T c0 = sk * (fac - rk);           // S_K (rho*_K - rho_K)
+    f[0] += star ? c0 : T(0);
 #pragma unroll
-        for (int e = 0; e < ND; ++e) {
-            const T ustar_e = (e == D) ? fac * sstar : fac * vk[e];
-            f[1 + e] += sk * (ustar_e - rk * vk[e]);
-        }
-        f[NV - 1] += sk * (e_star - Ek);
+    for (int e = 0; e < ND; ++e) {
+        // transverse: S_K (rho*_K - rho_K) v_e; normal: S_K (rho*_K S* - rho_K u_K)
+        const T ce = (e == D) ? sk * (fac * sstar - mflux) : c0 * vk[e];
+        f[1 + e] += star ? ce : T(0);
     }
+    const T cE = sk * (e_star - Ek);
+    f[NV - 1] += star ? cE : T(0);
 }
 
 // Mirror image of a face state across a wall normal to axis D.

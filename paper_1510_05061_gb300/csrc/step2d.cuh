@@ -153,30 +153,59 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     }
     __syncthreads();
 
-    // ---- face fluxes
-    for (int i = tid; i < (TX + 1) * TY; i += NT) {
-        const int fi = i % (TX + 1), cy = i / (TX + 1);
-        T wl[NV], wr[NV], f[NV];
+    // ---- face fluxes: the low x and low y faces of each thread's own cell
+    // in one straight-line block, then the high-side faces of the tile.
+    // Reflecting walls replace the far-side state by the mirror of the near
+    // side's (by selects); a ragged tile's first cell past the domain has
+    // the high wall as its low face.
+    {
+        T wlx[NV], wrx[NV], wly[NV], wry[NV], fxv[NV], fyv[NV];
+        const bool xw_lo = x0 + tx == 0 && a.bc_lo[0] == BC_REFLECT;
+        const bool xw_hi = x0 + tx == nx && a.bc_hi[0] == BC_REFLECT;
+        const bool yw_lo = y0 + ty == 0 && a.bc_lo[1] == BC_REFLECT;
+        const bool yw_hi = y0 + ty == ny && a.bc_hi[1] == BC_REFLECT;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) { wl[q] = WX(wxh, q, cy, fi - 1); wr[q] = WX(wxl, q, cy, fi); }
-        const int gf = x0 + fi;
-        if (gf == 0 && a.bc_lo[0] == BC_REFLECT) mirror_state<T, NV, 0>(wr, wl);
-        if (gf == nx && a.bc_hi[0] == BC_REFLECT) mirror_state<T, NV, 0>(wl, wr);
-        hllc<T, ND, 0, false>(wl, wr, T(0), T(0), gam, igm1, f);
+        for (int q = 0; q < NV; ++q) {
+            const T xl = WX(wxh, q, ty, tx - 1), xr = WX(wxl, q, ty, tx);
+            wlx[q] = xw_lo ? (q == 1 ? -xr : xr) : xl;
+            wrx[q] = xw_hi ? (q == 1 ? -xl : xl) : xr;
+            const T yl = WY(wyh, q, ty - 1, tx), yr = WY(wyl, q, ty, tx);
+            wly[q] = yw_lo ? (q == 2 ? -yr : yr) : yl;
+            wry[q] = yw_hi ? (q == 2 ? -yl : yl) : yr;
+        }
+        hllc<T, ND, 0, false>(wlx, wrx, T(0), T(0), gam, igm1, fxv);
+        hllc<T, ND, 1, false>(wly, wry, T(0), T(0), gam, igm1, fyv);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
+        for (int q = 0; q < NV; ++q) {
+            FX(q, ty, tx) = fxv[q];
+            FY(q, ty, tx) = fyv[q];
+        }
     }
-    for (int i = tid; i < TX * (TY + 1); i += NT) {
-        const int cx = i % TX, fi = i / TX;
+    if (tid < TY + TX) {
+        const bool isx = tid < TY;
+        const int r = isx ? tid : tid - TY;
         T wl[NV], wr[NV], f[NV];
+        if (isx) {
+            const bool wall = x0 + TX == nx && a.bc_hi[0] == BC_REFLECT;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) { wl[q] = WY(wyh, q, fi - 1, cx); wr[q] = WY(wyl, q, fi, cx); }
-        const int gf = y0 + fi;
-        if (gf == 0 && a.bc_lo[1] == BC_REFLECT) mirror_state<T, NV, 1>(wr, wl);
-        if (gf == ny && a.bc_hi[1] == BC_REFLECT) mirror_state<T, NV, 1>(wl, wr);
-        hllc<T, ND, 1, false>(wl, wr, T(0), T(0), gam, igm1, f);
+            for (int q = 0; q < NV; ++q) {
+                wl[q] = WX(wxh, q, r, TX - 1);
+                wr[q] = wall ? (q == 1 ? -wl[q] : wl[q]) : WX(wxl, q, r, TX);
+            }
+            hllc<T, ND, 0, false>(wl, wr, T(0), T(0), gam, igm1, f);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
+            for (int q = 0; q < NV; ++q) FX(q, r, TX) = f[q];
+        } else {
+            const bool wall = y0 + TY == ny && a.bc_hi[1] == BC_REFLECT;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                wl[q] = WY(wyh, q, TY - 1, r);
+                wr[q] = wall ? (q == 2 ? -wl[q] : wl[q]) : WY(wyl, q, TY, r);
+            }
+            hllc<T, ND, 1, false>(wl, wr, T(0), T(0), gam, igm1, f);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) FY(q, TY, r) = f[q];
+        }
     }
     __syncthreads();
 

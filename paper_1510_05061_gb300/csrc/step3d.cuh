@@ -21,6 +21,13 @@
 
 #include "hydro_device.cuh"
 
+// Build option: keep the next plane's global loads in flight in registers
+// (FP32 only).  Off by default: measured on GB300 it raises register
+// pressure under the two-CTA bound and costs more than it hides.
+#ifndef HYDRO_PREFETCH
+#define HYDRO_PREFETCH 0
+#endif
+
 namespace hydro {
 
 template <typename T, bool HSE, int TX, int TY>
@@ -67,7 +74,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     constexpr int ND = 3, NV = 5, NT = TX * TY;
     // FP32 keeps the next plane's loads in flight; FP64 is bound by its
     // arithmetic pipe and has no registers to spare for them
-    constexpr bool PREFETCH = sizeof(T) == 4;
+    constexpr bool PREFETCH = HYDRO_PREFETCH && sizeof(T) == 4;
     using S = Step3DSmem<T, HSE, TX, TY>;
     constexpr int HX = S::HX, HY = S::HY;
     T *prim = reinterpret_cast<T *>(smem_raw);
@@ -193,6 +200,21 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         }
         __syncthreads();
         const bool xy = (p >= z0 && p < z1);
+        // the plane completed at the end of this iteration is p-1: start its
+        // own-cell loads now so that they overlap the half step and fluxes
+        const bool fin = p > z0 && own;
+        T ufin[NV];
+        T bgB = T(0), bgR = T(0), bgP = T(0);
+        if (fin) {
+            const size_t c = (size_t)(p - 1) * a.plane + (size_t)gy * nx + gx;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) ufin[q] = U[c + q * vs];
+            if constexpr (HSE) {
+                bgB = bgT[p + 1].B;
+                bgR = bgT[p + 1].rho_c;
+                bgP = bgT[p + 1].p_c;
+            }
+        }
 
         // ---- step 2: half step; own cell first (z faces kept in registers)
         T zlo[NV], ztop[NV];
@@ -246,54 +268,130 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         }
         __syncthreads();
 
-        // ---- step 3: face fluxes
+        // ---- step 3: face fluxes.  Each thread evaluates the low x face and
+        // the low y face of its own cell and the z face p - 1/2 of its
+        // column as one straight-line block (three independent HLLC solves
+        // the scheduler can interleave); the TY + TX high-side faces of the
+        // tile follow in a short second pass.  Reflecting walls replace the
+        // far-side state by the mirror of the near side's (by selects).
         const T rb_c = HSE ? bgT[p + 2].rho_c : T(0);
         const T pb_c = HSE ? bgT[p + 2].p_c : T(0);
-        if (xy) {
-            for (int i = tid; i < (TX + 1) * TY; i += NT) {
-                const int fi = i % (TX + 1), cy = i / (TX + 1);
-                T wl[NV], wr[NV], f[NV];
+        const T rb_f = HSE ? bgT[p + 2].rho_f : T(0);
+        const T pb_f = HSE ? bgT[p + 2].p_f : T(0);
+        const bool wall_zlo = p == 0 && a.bc_lo[2] == BC_REFLECT;
+        const bool wall_zhi = p == nz && a.bc_hi[2] == BC_REFLECT;
+        auto z_states = [&](T (&wl)[NV], T (&wr)[NV]) {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) { wl[q] = WX(wxh, q, cy, fi - 1); wr[q] = WX(wxl, q, cy, fi); }
-                const int gf = x0 + fi;
-                if (gf == 0 && a.bc_lo[0] == BC_REFLECT) mirror_state<T, NV, 0>(wr, wl);
-                if (gf == nx && a.bc_hi[0] == BC_REFLECT) mirror_state<T, NV, 0>(wl, wr);
-                hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
+            for (int q = 0; q < NV; ++q) {
+                const T sgn = q == 3 ? T(-1) : T(1);
+                wl[q] = wall_zlo ? sgn * zlo[q] : ztop_prev[q];
+                wr[q] = wall_zhi ? sgn * ztop_prev[q] : zlo[q];
             }
-            for (int i = tid; i < TX * (TY + 1); i += NT) {
-                const int cx = i % TX, fi = i / TX;
-                T wl[NV], wr[NV], f[NV];
-#pragma unroll
-                for (int q = 0; q < NV; ++q) { wl[q] = WY(wyh, q, fi - 1, cx); wr[q] = WY(wyl, q, fi, cx); }
-                const int gf = y0 + fi;
-                if (gf == 0 && a.bc_lo[1] == BC_REFLECT) mirror_state<T, NV, 1>(wr, wl);
-                if (gf == ny && a.bc_hi[1] == BC_REFLECT) mirror_state<T, NV, 1>(wl, wr);
-                hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
-            }
-        }
+        };
         T fz[NV];
-        if (p >= z0) {
-            // z face p - 1/2 between the top of cell p-1 and the bottom of cell p
-            T wl[NV], wr[NV];
-            if (p == 0 && a.bc_lo[2] == BC_REFLECT) {
+        if constexpr (sizeof(T) == 8) {
+            // FP64 is register-bound (one CTA per SM): one face at a time
+            if (xy) {
+                for (int i = tid; i < (TX + 1) * TY; i += NT) {
+                    const int fi = i % (TX + 1), cy = i / (TX + 1);
+                    T wl[NV], wr[NV], f[NV];
+                    const int gf = x0 + fi;
+                    const bool w_lo = gf == 0 && a.bc_lo[0] == BC_REFLECT;
+                    const bool w_hi = gf == nx && a.bc_hi[0] == BC_REFLECT;
 #pragma unroll
-                for (int q = 0; q < NV; ++q) wr[q] = zlo[q];
-                mirror_state<T, NV, 2>(wr, wl);
-            } else if (p == nz && a.bc_hi[2] == BC_REFLECT) {
+                    for (int q = 0; q < NV; ++q) {
+                        const T xl = WX(wxh, q, cy, fi - 1), xr = WX(wxl, q, cy, fi);
+                        wl[q] = w_lo ? (q == 1 ? -xr : xr) : xl;
+                        wr[q] = w_hi ? (q == 1 ? -xl : xl) : xr;
+                    }
+                    hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) wl[q] = ztop_prev[q];
-                mirror_state<T, NV, 2>(wl, wr);
+                    for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
+                }
+                for (int i = tid; i < TX * (TY + 1); i += NT) {
+                    const int cx = i % TX, fi = i / TX;
+                    T wl[NV], wr[NV], f[NV];
+                    const int gf = y0 + fi;
+                    const bool w_lo = gf == 0 && a.bc_lo[1] == BC_REFLECT;
+                    const bool w_hi = gf == ny && a.bc_hi[1] == BC_REFLECT;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        const T yl = WY(wyh, q, fi - 1, cx), yr = WY(wyl, q, fi, cx);
+                        wl[q] = w_lo ? (q == 2 ? -yr : yr) : yl;
+                        wr[q] = w_hi ? (q == 2 ? -yl : yl) : yr;
+                    }
+                    hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
+                }
+            }
+            if (p >= z0) {
+                T wlz[NV], wrz[NV];
+                z_states(wlz, wrz);
+                hllc<T, ND, 2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
             } else {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) { wl[q] = ztop_prev[q]; wr[q] = zlo[q]; }
+                for (int q = 0; q < NV; ++q) fz[q] = T(0);
             }
-            const T rb_f = HSE ? bgT[p + 2].rho_f : T(0);
-            const T pb_f = HSE ? bgT[p + 2].p_f : T(0);
-            hllc<T, ND, 2, HSE>(wl, wr, rb_f, pb_f, gam, igm1, fz);
+        } else if (xy) {
+            T wlx[NV], wrx[NV], wly[NV], wry[NV], wlz[NV], wrz[NV], fxv[NV], fyv[NV];
+            // the low face of this cell is a wall when it sits on the domain's
+            // low boundary, or on the high boundary (ragged tile: the cell is
+            // the first one past the domain)
+            const bool xw_lo = x0 + tx == 0 && a.bc_lo[0] == BC_REFLECT;
+            const bool xw_hi = x0 + tx == nx && a.bc_hi[0] == BC_REFLECT;
+            const bool yw_lo = y0 + ty == 0 && a.bc_lo[1] == BC_REFLECT;
+            const bool yw_hi = y0 + ty == ny && a.bc_hi[1] == BC_REFLECT;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const T xl = WX(wxh, q, ty, tx - 1), xr = WX(wxl, q, ty, tx);
+                wlx[q] = xw_lo ? (q == 1 ? -xr : xr) : xl;
+                wrx[q] = xw_hi ? (q == 1 ? -xl : xl) : xr;
+                const T yl = WY(wyh, q, ty - 1, tx), yr = WY(wyl, q, ty, tx);
+                wly[q] = yw_lo ? (q == 2 ? -yr : yr) : yl;
+                wry[q] = yw_hi ? (q == 2 ? -yl : yl) : yr;
+            }
+            z_states(wlz, wrz);
+            hllc<T, ND, 0, HSE>(wlx, wrx, rb_c, pb_c, gam, igm1, fxv);
+            hllc<T, ND, 1, HSE>(wly, wry, rb_c, pb_c, gam, igm1, fyv);
+            hllc<T, ND, 2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                FX(q, ty, tx) = fxv[q];
+                FY(q, ty, tx) = fyv[q];
+            }
+            // high-side faces of the tile: x face TX of each row, y face TY
+            // of each column
+            if (tid < TY + TX) {
+                const bool isx = tid < TY;
+                const int r = isx ? tid : tid - TY;
+                T wl[NV], wr[NV], f[NV];
+                if (isx) {
+                    const bool wall = x0 + TX == nx && a.bc_hi[0] == BC_REFLECT;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        wl[q] = WX(wxh, q, r, TX - 1);
+                        wr[q] = wall ? (q == 1 ? -wl[q] : wl[q]) : WX(wxl, q, r, TX);
+                    }
+                    hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) FX(q, r, TX) = f[q];
+                } else {
+                    const bool wall = y0 + TY == ny && a.bc_hi[1] == BC_REFLECT;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        wl[q] = WY(wyh, q, TY - 1, r);
+                        wr[q] = wall ? (q == 2 ? -wl[q] : wl[q]) : WY(wyl, q, TY, r);
+                    }
+                    hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) FY(q, TY, r) = f[q];
+                }
+            }
+        } else if (p == z1) {
+            T wlz[NV], wrz[NV];
+            z_states(wlz, wrz);
+            hllc<T, ND, 2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
         } else {
 #pragma unroll
             for (int q = 0; q < NV; ++q) fz[q] = T(0);
@@ -301,12 +399,12 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         __syncthreads();
 
         // ---- step 4: complete plane p-1 (an output plane when p > z0)
-        if (p > z0 && own) {
+        if (fin) {
             const int k = p - 1;
             const size_t c = (size_t)k * a.plane + (size_t)gy * nx + gx;
             T u[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) u[q] = U[c + q * vs];
+            for (int q = 0; q < NV; ++q) u[q] = ufin[q];
             T du[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) du[q] = -(div_prev[q] + (fz[q] - fz_prev[q]) * inv_dx[2]);
@@ -318,18 +416,18 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 T src = grav[d] * rsum;
-                if (HSE && d == 2) src -= bgT[k + 2].B;
+                if (HSE && d == 2) src -= bgB;
                 u[1 + d] += dt * (du[1 + d] + src);
             }
             u[4] += dt * (du[4] + msrc);
 #pragma unroll
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
             // CFL signal speed and admissibility of the new state
-            const T rho = HSE ? bgT[k + 2].rho_c + u[0] : u[0];
+            const T rho = HSE ? bgR + u[0] : u[0];
             const T rinv = rcp_t(rho);
             const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
             const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
-            const T pres = HSE ? bgT[k + 2].p_c + pp : pp;
+            const T pres = HSE ? bgP + pp : pp;
             const T gp = gam * pres;
             const T cs = gp * rsqrt_t(gp * rho);
             const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
