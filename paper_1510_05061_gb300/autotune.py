@@ -93,13 +93,77 @@ def tune_batch(batch, steps: int = 4, zchunks: Iterable[int] = DEFAULT_ZCHUNKS,
     best = None
     for v in variants:
         for z in zchunks:
-            batch.configure(v, z)
+            try:
+                batch.configure(v, z)
+            except hydro.HydroError:             # shape not available in this precision
+                break
             batch.step(2)                        # first launch of this kernel, warm caches
             ms = time_steps(batch, steps)
             table.append({"variant": v, "tile": list(shapes[v]), "zchunk": z, "ms_per_step": ms})
             if best is None or ms < best["ms_per_step"]:
                 best = table[-1]
     batch.configure(best["variant"], best["zchunk"])
+    choice = {"variant": best["variant"], "tile": best["tile"], "zchunk": best["zchunk"],
+              "ms_per_step": best["ms_per_step"], "table": table}
+    if use_cache:
+        cache[key] = choice
+        _store_cache(cache)
+    return dict(choice, cached=False)
+
+
+def sim_signature(sim) -> str:
+    import torch
+
+    p = sim.prob
+    prec = "fp32" if p.precision == inputs.FP32 else "fp64"
+    return f"{torch.cuda.get_device_name()}|single|{prec}|hse{p.hse_subtract}|n={p.n[0]}x{p.n[1]}x{p.n[2]}"
+
+
+def time_sim_steps(sim, steps: int) -> float:
+    import torch
+
+    s = sim.stream
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    sim.run_steps(steps)
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (8, 16, 32, 64),
+                    variants: Optional[Iterable[int]] = None, use_cache: bool = True) -> dict:
+    """Configure a single 3D solve with its fastest (tile shape, z-chunk).
+    Tuning advances the solve by the steps it times."""
+    from . import hydro
+
+    if sim.prob.ndim != 3:
+        return {"variant": 0, "tile": [32, 8], "zchunk": 1, "cached": False, "table": []}
+    key = sim_signature(sim)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        ch = cache[key]
+        sim.configure(ch["variant"], ch["zchunk"])
+        return dict(ch, cached=True)
+    shapes = hydro.batch_variants()
+    variants = list(range(len(shapes))) if variants is None else list(variants)
+    table, best = [], None
+    for v in variants:
+        for z in zchunks:
+            if z > sim.prob.n[2]:
+                continue
+            try:
+                sim.configure(v, z)
+            except hydro.HydroError:
+                break
+            sim.run_steps(2)
+            ms = time_sim_steps(sim, steps)
+            table.append({"variant": v, "tile": list(shapes[v]), "zchunk": z, "ms_per_step": ms})
+            if best is None or ms < best["ms_per_step"]:
+                best = table[-1]
+    sim.configure(best["variant"], best["zchunk"])
     choice = {"variant": best["variant"], "tile": best["tile"], "zchunk": best["zchunk"],
               "ms_per_step": best["ms_per_step"], "table": table}
     if use_cache:

@@ -1,5 +1,5 @@
-// batch3d.cu -- instantiations of the persistent batched 3D step for every
-// tile shape the autotuner may choose, both precisions and both modes.
+// batch3d_f32.cu -- FP32 instantiations of the persistent batched 3D step
+// for every tile shape the autotuner may choose, both modes.
 #include "launchers.h"
 #include "step3d.cuh"
 
@@ -52,46 +52,43 @@ struct Batch3D {
     static int max_grid() { return ensure() == cudaSuccess ? grid_cap() : 0; }
 };
 
-template <typename T, bool HSE>
+template <bool HSE>
 cudaError_t launch_v(int v, const BatchInst *insts, const BatchItem *items, int nitems, int parity,
                      int grid, cudaStream_t s)
 {
     switch (v) {
-    case 0: return Batch3D<T, HSE, 32, 8>::launch(insts, items, nitems, parity, grid, s);
-    case 1: return Batch3D<T, HSE, 32, 4>::launch(insts, items, nitems, parity, grid, s);
-    default: return Batch3D<T, HSE, 16, 16>::launch(insts, items, nitems, parity, grid, s);
+    case 0: return Batch3D<float, HSE, 32, 8>::launch(insts, items, nitems, parity, grid, s);
+    case 1: return Batch3D<float, HSE, 32, 4>::launch(insts, items, nitems, parity, grid, s);
+    case 2: return Batch3D<float, HSE, 16, 16>::launch(insts, items, nitems, parity, grid, s);
+    case 3: return Batch3D<float, HSE, 32, 16>::launch(insts, items, nitems, parity, grid, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, bool HSE>
+template <bool HSE>
 int grid_v(int v)
 {
     switch (v) {
-    case 0: return Batch3D<T, HSE, 32, 8>::max_grid();
-    case 1: return Batch3D<T, HSE, 32, 4>::max_grid();
-    default: return Batch3D<T, HSE, 16, 16>::max_grid();
+    case 0: return Batch3D<float, HSE, 32, 8>::max_grid();
+    case 1: return Batch3D<float, HSE, 32, 4>::max_grid();
+    case 2: return Batch3D<float, HSE, 16, 16>::max_grid();
+    case 3: return Batch3D<float, HSE, 32, 16>::max_grid();
+    default: return 0;
     }
 }
 
 }  // namespace
 
-static_assert(BATCH3D_SHAPES[0].tx == 32 && BATCH3D_SHAPES[0].ty == 8, "variant table");
-static_assert(BATCH3D_SHAPES[1].tx == 32 && BATCH3D_SHAPES[1].ty == 4, "variant table");
-static_assert(BATCH3D_SHAPES[2].tx == 16 && BATCH3D_SHAPES[2].ty == 16, "variant table");
-
-cudaError_t launch_batch3d(int variant, bool fp32, bool hse, const BatchInst *insts,
-                           const BatchItem *items, int nitems, int parity, int grid, cudaStream_t s)
+cudaError_t launch_batch3d_f32(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
+                               int nitems, int parity, int grid, cudaStream_t s)
 {
-    if (fp32) return hse ? launch_v<float, true>(variant, insts, items, nitems, parity, grid, s)
-                         : launch_v<float, false>(variant, insts, items, nitems, parity, grid, s);
-    return hse ? launch_v<double, true>(variant, insts, items, nitems, parity, grid, s)
-               : launch_v<double, false>(variant, insts, items, nitems, parity, grid, s);
+    return hse ? launch_v<true>(variant, insts, items, nitems, parity, grid, s)
+               : launch_v<false>(variant, insts, items, nitems, parity, grid, s);
 }
 
-int batch3d_max_grid(int variant, bool fp32, bool hse)
+int batch3d_max_grid_f32(int variant, bool hse)
 {
-    if (fp32) return hse ? grid_v<float, true>(variant) : grid_v<float, false>(variant);
-    return hse ? grid_v<double, true>(variant) : grid_v<double, false>(variant);
+    return hse ? grid_v<true>(variant) : grid_v<false>(variant);
 }
 
 }  // namespace hydro

@@ -1,0 +1,92 @@
+// batch3d_f64.cu -- FP64 instantiations of the persistent batched 3D step
+// for every tile shape the autotuner may choose, both modes.
+#include "launchers.h"
+#include "step3d.cuh"
+
+namespace hydro {
+
+namespace {
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename K>
+cudaError_t prepare(K kernel, size_t smem, int threads, int *max_grid)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    *max_grid = (nb > 0 ? nb : 1) * sm_count();
+    return cudaSuccess;
+}
+
+template <typename T, bool HSE, int TX, int TY>
+struct Batch3D {
+    static int &grid_cap() { static int g = 0; return g; }
+    static cudaError_t ensure()
+    {
+        if (grid_cap()) return cudaSuccess;
+        return prepare(step3d_batch_kernel<T, HSE, TX, TY>, Step3DSmem<T, HSE, TX, TY>::bytes, TX * TY,
+                       &grid_cap());
+    }
+    static cudaError_t launch(const BatchInst *insts, const BatchItem *items, int nitems, int parity,
+                              int grid, cudaStream_t s)
+    {
+        cudaError_t e = ensure();
+        if (e != cudaSuccess) return e;
+        step3d_batch_kernel<T, HSE, TX, TY>
+            <<<grid, TX * TY, Step3DSmem<T, HSE, TX, TY>::bytes, s>>>(insts, items, nitems, parity);
+        return cudaGetLastError();
+    }
+    static int max_grid() { return ensure() == cudaSuccess ? grid_cap() : 0; }
+};
+
+template <bool HSE>
+cudaError_t launch_v(int v, const BatchInst *insts, const BatchItem *items, int nitems, int parity,
+                     int grid, cudaStream_t s)
+{
+    switch (v) {
+    case 0: return Batch3D<double, HSE, 32, 8>::launch(insts, items, nitems, parity, grid, s);
+    case 1: return Batch3D<double, HSE, 32, 4>::launch(insts, items, nitems, parity, grid, s);
+    case 2: return Batch3D<double, HSE, 16, 16>::launch(insts, items, nitems, parity, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool HSE>
+int grid_v(int v)
+{
+    switch (v) {
+    case 0: return Batch3D<double, HSE, 32, 8>::max_grid();
+    case 1: return Batch3D<double, HSE, 32, 4>::max_grid();
+    case 2: return Batch3D<double, HSE, 16, 16>::max_grid();
+    default: return 0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch3d_f64(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
+                               int nitems, int parity, int grid, cudaStream_t s)
+{
+    return hse ? launch_v<true>(variant, insts, items, nitems, parity, grid, s)
+               : launch_v<false>(variant, insts, items, nitems, parity, grid, s);
+}
+
+int batch3d_max_grid_f64(int variant, bool hse)
+{
+    return hse ? grid_v<true>(variant) : grid_v<false>(variant);
+}
+
+}  // namespace hydro

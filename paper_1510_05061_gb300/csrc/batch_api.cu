@@ -32,9 +32,9 @@ size_t max_items_of(const hydro_problem &p)
 {
     if (p.ndim == 2) return (size_t)tiles_along(p.n[0], BATCH2D_TX) * tiles_along(p.n[1], BATCH2D_TY);
     size_t m = 0;
-    for (int v = 0; v < BATCH3D_VARIANTS; ++v)
-        m = std::max(m, (size_t)tiles_along(p.n[0], BATCH3D_SHAPES[v].tx) *
-                            tiles_along(p.n[1], BATCH3D_SHAPES[v].ty) * p.n[2]);
+    for (int v = 0; v < TILE3D_VARIANTS; ++v)
+        m = std::max(m, (size_t)tiles_along(p.n[0], TILE3D_SHAPES[v].tx) *
+                            tiles_along(p.n[1], TILE3D_SHAPES[v].ty) * p.n[2]);
     return m;
 }
 
@@ -182,7 +182,7 @@ int effective_zchunk(const hydro_batch *b)
 // capture the two-launch (both parities) graph.
 int rebuild(hydro_batch *b)
 {
-    const TileShape ts = BATCH3D_SHAPES[b->variant];
+    const TileShape ts = TILE3D_SHAPES[b->variant];
     const int zdef = effective_zchunk(b);
     b->host_insts.assign(b->max_instances, BatchInst{});
     b->host_items3.clear();
@@ -501,7 +501,7 @@ int hydro_batch_init(const hydro_problem *probs, int count, void *const *Ua, voi
 
 int hydro_batch_configure(hydro_batch *b, int variant, int zchunk)
 {
-    if (!b || variant < 0 || variant >= BATCH3D_VARIANTS || zchunk < 0) return HYDRO_ERR_INVALID_ARG;
+    if (!b || !tile3d_available(variant, b->precision == HYDRO_FP32) || zchunk < 0) return HYDRO_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
     b->variant = variant;
     b->zchunk = zchunk;
@@ -510,9 +510,9 @@ int hydro_batch_configure(hydro_batch *b, int variant, int zchunk)
 
 int hydro_batch_variant_shape(int variant, int *tx, int *ty)
 {
-    if (variant < 0 || variant >= BATCH3D_VARIANTS || !tx || !ty) return HYDRO_ERR_INVALID_ARG;
-    *tx = BATCH3D_SHAPES[variant].tx;
-    *ty = BATCH3D_SHAPES[variant].ty;
+    if (variant < 0 || variant >= TILE3D_VARIANTS || !tx || !ty) return HYDRO_ERR_INVALID_ARG;
+    *tx = TILE3D_SHAPES[variant].tx;
+    *ty = TILE3D_SHAPES[variant].ty;
     return HYDRO_OK;
 }
 

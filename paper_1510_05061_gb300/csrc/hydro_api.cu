@@ -32,6 +32,7 @@ struct hydro_sim {
     cudaStream_t stream;
     double dx[3], inv_dx[3], cell_volume;
     int tiles_x, tiles_y;
+    int variant;             // 3D tile shape (TILE3D_SHAPES index)
     int zchunk;
     long launches;
     int err_state;           // sticky host-side copy of a non-physical error
@@ -83,8 +84,12 @@ int step_max_ctas(const hydro_problem *p)
 {
     if (p->ndim == 2)
         return tiles_along(p->n[0], STEP2D_TX) * tiles_along(p->n[1], STEP2D_TY);
-    // zchunk >= 1: at most nz chunks
-    return tiles_along(p->n[0], STEP3D_TX) * tiles_along(p->n[1], STEP3D_TY) * p->n[2];
+    // any tile shape, zchunk >= 1: at most nz chunks
+    int m = 0;
+    for (int v = 0; v < TILE3D_VARIANTS; ++v)
+        m = std::max(m, tiles_along(p->n[0], TILE3D_SHAPES[v].tx) * tiles_along(p->n[1], TILE3D_SHAPES[v].ty) *
+                            p->n[2]);
+    return m;
 }
 
 WorkLayout layout(const hydro_problem *p)
@@ -182,8 +187,8 @@ int launch_step(hydro_sim *s, double t_end)
     } else {
         const int nch = (s->prob.n[2] + s->zchunk - 1) / s->zchunk;
         dim3 grid(s->tiles_x * s->tiles_y, nch);
-        e = fp32 ? launch_step3d_f32(a, grid, s->stream, s->prob.hse_subtract != 0)
-                 : launch_step3d_f64(a, grid, s->stream, s->prob.hse_subtract != 0);
+        e = fp32 ? launch_step3d_f32(s->variant, a, grid, s->stream, s->prob.hse_subtract != 0)
+                 : launch_step3d_f64(s->variant, a, grid, s->stream, s->prob.hse_subtract != 0);
     }
     s->launches += 1;
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
@@ -284,8 +289,9 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
         s->tiles_x = tiles_along(prob->n[0], STEP2D_TX);
         s->tiles_y = tiles_along(prob->n[1], STEP2D_TY);
     } else {
-        s->tiles_x = tiles_along(prob->n[0], STEP3D_TX);
-        s->tiles_y = tiles_along(prob->n[1], STEP3D_TY);
+        s->variant = 0;
+        s->tiles_x = tiles_along(prob->n[0], TILE3D_SHAPES[0].tx);
+        s->tiles_y = tiles_along(prob->n[1], TILE3D_SHAPES[0].ty);
     }
     s->zchunk = default_zchunk(s);
 
@@ -484,6 +490,17 @@ int hydro_set_zchunk(hydro_sim *s, int zchunk)
     if (!s || zchunk < 0) return HYDRO_ERR_INVALID_ARG;
     if (s->prob.ndim == 2) return zchunk <= 1 ? HYDRO_OK : HYDRO_ERR_INVALID_ARG;
     s->zchunk = zchunk == 0 ? default_zchunk(s) : std::min(zchunk, s->prob.n[2]);
+    return HYDRO_OK;
+}
+
+int hydro_set_tile(hydro_sim *s, int variant)
+{
+    if (!s) return HYDRO_ERR_INVALID_ARG;
+    if (s->prob.ndim == 2) return variant == 0 ? HYDRO_OK : HYDRO_ERR_INVALID_ARG;
+    if (!tile3d_available(variant, s->prob.precision == HYDRO_FP32)) return HYDRO_ERR_INVALID_ARG;
+    s->variant = variant;
+    s->tiles_x = tiles_along(s->prob.n[0], TILE3D_SHAPES[variant].tx);
+    s->tiles_y = tiles_along(s->prob.n[1], TILE3D_SHAPES[variant].ty);
     return HYDRO_OK;
 }
 

@@ -8,30 +8,45 @@
 
 namespace hydro {
 
-// 3D step tile: TX x TY threads, one column of cells each.
-constexpr int STEP3D_TX = 32;
-constexpr int STEP3D_TY = 8;
 // 2D step tile.
 constexpr int STEP2D_TX = 32;
 constexpr int STEP2D_TY = 8;
 
-// Tile shapes of the batched 3D step (chosen per batch by the autotuner).
+// Tile shapes of the 3D step (TX x TY threads, one column of cells each),
+// chosen per solve or per batch by the autotuner.  The 512-thread 32 x 16
+// tile is FP32 only: an FP64 thread needs about twice the 128 registers a
+// 512-thread CTA can have.
 struct TileShape { int tx, ty; };
-constexpr int BATCH3D_VARIANTS = 3;
-constexpr TileShape BATCH3D_SHAPES[BATCH3D_VARIANTS] = {{32, 8}, {32, 4}, {16, 16}};
+constexpr int TILE3D_VARIANTS = 4;
+constexpr TileShape TILE3D_SHAPES[TILE3D_VARIANTS] = {{32, 8}, {32, 4}, {16, 16}, {32, 16}};
+inline bool tile3d_available(int v, bool fp32) { return v >= 0 && v < TILE3D_VARIANTS && (v != 3 || fp32); }
 constexpr int BATCH2D_TX = 32, BATCH2D_TY = 8;
 
 // Persistent batched steps over a device work list; `grid` CTAs walk the
 // items.  *_max_grid: resident CTAs on the current device (SMs x occupancy).
-cudaError_t launch_batch3d(int variant, bool fp32, bool hse, const BatchInst *insts,
-                           const BatchItem *items, int nitems, int parity, int grid, cudaStream_t s);
+cudaError_t launch_batch3d_f32(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
+                               int nitems, int parity, int grid, cudaStream_t s);
+cudaError_t launch_batch3d_f64(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
+                               int nitems, int parity, int grid, cudaStream_t s);
+int batch3d_max_grid_f32(int variant, bool hse);
+int batch3d_max_grid_f64(int variant, bool hse);
+inline cudaError_t launch_batch3d(int variant, bool fp32, bool hse, const BatchInst *insts,
+                                  const BatchItem *items, int nitems, int parity, int grid, cudaStream_t s)
+{
+    return fp32 ? launch_batch3d_f32(variant, hse, insts, items, nitems, parity, grid, s)
+                : launch_batch3d_f64(variant, hse, insts, items, nitems, parity, grid, s);
+}
 cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, const BatchItem *items, int nitems,
                            int parity, int grid, cudaStream_t s);
-int batch3d_max_grid(int variant, bool fp32, bool hse);
+inline int batch3d_max_grid(int variant, bool fp32, bool hse)
+{
+    return fp32 ? batch3d_max_grid_f32(variant, hse) : batch3d_max_grid_f64(variant, hse);
+}
 int batch2d_max_grid(bool fp32);
 
-cudaError_t launch_step3d_f64(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
-cudaError_t launch_step3d_f32(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
+// single-solve 3D step with tile variant v (grid = tiles x z-chunks)
+cudaError_t launch_step3d_f64(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
+cudaError_t launch_step3d_f32(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
 cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32);
 
 // Auxiliary kernels (aux.cu).  fp32 selects the stored precision.

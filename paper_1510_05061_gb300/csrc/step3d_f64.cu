@@ -1,16 +1,18 @@
-// step3d_f64.cu -- FP64 instantiations of the fused 3D step.
+// step3d_f64.cu -- FP64 instantiations of the fused single-solve 3D step
+// for every tile shape.
 #include "launchers.h"
 #include "step3d.cuh"
 
 namespace hydro {
 
-template <typename T, bool HSE>
-static cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
+namespace {
+
+template <typename T, bool HSE, int TX, int TY>
+cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
-    constexpr int TX = STEP3D_TX, TY = STEP3D_TY;
     auto k = step3d_kernel<T, HSE, TX, TY>;
     constexpr size_t smem = Step3DSmem<T, HSE, TX, TY>::bytes;
-    static bool configured = false;   // per process; the attribute is per function
+    static bool configured = false;   // the attribute is per function
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -20,9 +22,22 @@ static cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step3d_f64(const StepArgs &a, dim3 grid, cudaStream_t s, bool hse)
+template <bool HSE>
+cudaError_t launch_v(int v, const StepArgs &a, dim3 grid, cudaStream_t s)
 {
-    return hse ? launch3d<double, true>(a, grid, s) : launch3d<double, false>(a, grid, s);
+    switch (v) {
+    case 0: return launch3d<double, HSE, 32, 8>(a, grid, s);
+    case 1: return launch3d<double, HSE, 32, 4>(a, grid, s);
+    case 2: return launch3d<double, HSE, 16, 16>(a, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_step3d_f64(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse)
+{
+    return hse ? launch_v<true>(v, a, grid, s) : launch_v<false>(v, a, grid, s);
 }
 
 }  // namespace hydro

@@ -43,7 +43,7 @@ HYDRO_RED_DT_LAST = 6
 EXPORTS = (
     "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_step",
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
-    "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk",
+    "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk", "hydro_set_tile",
     "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
     "hydro_selftest_math", "hydro_batch_workspace_bytes", "hydro_batch_init",
     "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH):
     L.hydro_debug_poke.argtypes = [vp, C.c_int, C.c_long, C.c_double]
     L.hydro_set_zchunk.restype = C.c_int
     L.hydro_set_zchunk.argtypes = [vp, C.c_int]
+    L.hydro_set_tile.restype = C.c_int
+    L.hydro_set_tile.argtypes = [vp, C.c_int]
     L.hydro_launch_count.restype = C.c_long
     L.hydro_launch_count.argtypes = [vp]
     L.hydro_destroy.restype = C.c_int
@@ -393,6 +395,14 @@ class Simulation:
 
     def set_zchunk(self, z: int):
         hydro_set_zchunk(self.h, z)
+
+    def set_tile(self, variant: int):
+        _check(load().hydro_set_tile(self.h, int(variant)), "hydro_set_tile")
+
+    def configure(self, variant: int, zchunk: int = 0):
+        """Tile shape and z-chunk of the 3D step (the autotuner's knobs)."""
+        self.set_tile(variant)
+        self.set_zchunk(zchunk)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -121,3 +121,16 @@ def test_batch_with_hse_instances(hy):
     for i, (ref, t, n) in enumerate(solo):
         assert np.array_equal(batch_state(hy, b, i), ref), i
     b.close()
+
+
+def test_fp32_batch_all_tiles_equal_solo(hy):
+    items = [inputs.kelvin_helmholtz(n, ndim=3, U=1.1, ratio=2.0, instance=i) for i, n in enumerate((21, 34, 40))]
+    items.append(inputs.kelvin_helmholtz(90, ndim=2, U=1.4, ratio=3.0, instance=9))
+    solo = solo_states(hy, items, 6)
+    for v in (0, 1, 2, 3):
+        b = hy.Batch(items)
+        b.configure(v, 9)
+        b.step(6)
+        for i, (ref, t, n) in enumerate(solo):
+            assert np.array_equal(b.get_state(i), ref), (v, i)
+        b.close()

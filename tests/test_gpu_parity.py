@@ -343,3 +343,25 @@ def test_fp32_rt_linear_phase_density_error(hy):
         sim.close()
     err = l1rel(rho[inputs.FP32], rho[inputs.FP64])
     assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("prec,variants", [(inputs.FP64, (0, 1, 2)), (inputs.FP32, (0, 1, 2, 3))])
+def test_tile_shape_invariance_bitwise(hy, prec, variants):
+    """Every tile shape the autotuner may pick gives the same bits (ragged
+    sizes, reflecting walls, hydrostatic mode)."""
+    prob, W = inputs.rayleigh_taylor(37, nz=45, amplitude=0.05, hse_subtract=1, precision=prec)
+    prob = prob.replace(n=(37, 37, 45))
+    outs = []
+    for v in variants:
+        sim = hy.Simulation(prob, W)
+        sim.configure(v, 7)
+        sim.run_steps(4)
+        outs.append(sim.get_state())
+        sim.close()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    if prec == inputs.FP64:
+        sim = hy.Simulation(prob, W)
+        with pytest.raises(hy.HydroError):
+            sim.set_tile(3)          # the 512-thread tile is FP32 only
+        sim.close()
