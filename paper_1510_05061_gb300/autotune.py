@@ -18,7 +18,7 @@ from typing import Dict, Iterable, Optional
 
 from . import inputs
 
-DEFAULT_ZCHUNKS = (4, 8, 16, 32)
+DEFAULT_ZCHUNKS = (8, 16, 32, 64)
 
 
 def cache_path() -> str:
@@ -133,7 +133,7 @@ def time_sim_steps(sim, steps: int) -> float:
     return a.elapsed_time(b) / steps
 
 
-def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (8, 16, 32, 64),
+def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 128),
                     variants: Optional[Iterable[int]] = None, use_cache: bool = True) -> dict:
     """Configure a single 3D solve with its fastest (tile shape, z-chunk).
     Tuning advances the solve by the steps it times."""

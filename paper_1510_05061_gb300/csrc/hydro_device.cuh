@@ -298,6 +298,26 @@ __device__ __forceinline__ double block_max(double v, double *red)
     return v;
 }
 
+// The same max taken in the working precision (max is exact in any
+// precision), widened to FP64 once: an FP32 step keeps the reduction off the
+// FP64 pipe.  red must hold 32 doubles.
+template <int NT, typename T>
+__device__ __forceinline__ double block_max_t(T v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    T *r = reinterpret_cast<T *>(red);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) r[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < NT / 32 ? r[lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return double(v);
+}
+
 // Last-CTA finalisation of a step's time control.  Each of the nblocks
 // contributions (CTAs, or work items of one instance) calls it once with its
 // max signal speed (valid in thread 0), whether any of its cells failed the

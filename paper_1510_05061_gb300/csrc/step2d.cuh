@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     bool bad;
     step2d_body<T, TX, TY>(a, blockIdx.x, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
-    const double m = block_max<NT>(double(smax), red);
+    const double m = block_max_t<NT, T>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd,
                     true, &s_last);
 }
@@ -295,7 +295,7 @@ step2d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
             bool bad;
             step2d_body<T, TX, TY>(sa, w.tile, dtd, smem_raw, smax, bad);
             const bool bad_cta = __syncthreads_or(bad) != 0;
-            const double m = block_max<NT>(double(smax), red);
+            const double m = block_max_t<NT, T>(smax, red);
             finish_step<NT>(m, bad_cta, sa, insts[w.inst].nitems, w.local, dtd, true, &s_last);
         }
         __syncthreads();

@@ -34,7 +34,11 @@ template <typename T, bool HSE, int TX, int TY>
 struct Step3DSmem {
     static constexpr int NV = 5;
     static constexpr int HX = TX + 4, HY = TY + 4;
-    static constexpr size_t prim = 3ull * NV * HY * HX;        // [3][NV][HY][HX]
+    // Row stride of the staged planes.  A warp of a 16-wide tile spans two
+    // rows; for 4-byte values a stride = 16 (mod 32) puts them on disjoint
+    // shared-memory banks.  (8-byte values take one wavefront per row.)
+    static constexpr int HXS = (TX == 16 && sizeof(T) == 4) ? 48 : HX;
+    static constexpr size_t prim = 3ull * NV * HY * HXS;       // [3][NV][HY][HXS]
     static constexpr size_t wx = (size_t)NV * TY * (TX + 2);   // [NV][TY][TX+2]
     static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;   // [NV][TY+2][TX]
     static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
@@ -98,8 +102,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(a.inv_dx[2])};
     const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(a.grav[2])};
 
+    constexpr int HXS = S::HXS;
     auto P = [&](int slot, int q, int hy, int hx) -> T & {
-        return prim[((size_t)(slot * NV + q) * HY + hy) * HX + hx];
+        return prim[((size_t)(slot * NV + q) * HY + hy) * HXS + hx];
     };
 
     // ---- stage plane pz (may be a ghost plane) into its ring slot, in two
@@ -471,7 +476,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
     bool bad;
     step3d_body<T, HSE, TX, TY>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
-    const double m = block_max<NT>(double(smax), red);
+    const double m = block_max_t<NT, T>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd,
                     true, &s_last);
 }
@@ -507,7 +512,7 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
             bool bad;
             step3d_body<T, HSE, TX, TY>(sa, w.tile, w.chunk, dtd, smem_raw, smax, bad);
             const bool bad_cta = __syncthreads_or(bad) != 0;
-            const double m = block_max<NT>(double(smax), red);
+            const double m = block_max_t<NT, T>(smax, red);
             finish_step<NT>(m, bad_cta, sa, insts[w.inst].nitems, w.local, dtd, true, &s_last);
         }
         __syncthreads();
