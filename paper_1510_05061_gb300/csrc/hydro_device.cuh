@@ -84,18 +84,24 @@ __device__ __forceinline__ float mc_slope(float dl, float dr)
     return (dl * dr > 0.0f) ? copysignf(a, dr) : 0.0f;
 }
 
-// FP64 form: the sign test and both minima act on the IEEE bit patterns
-// (for non-negative doubles integer order equals numeric order), leaving
-// three FP64 operations per slope: 2 min(|dl|,|dr|), dl + dr and the halving.
+// FP64 form: the sign test, both minima, the doubling and the halving act
+// on the IEEE bit patterns (integer pipe; for non-negative doubles integer
+// order is numeric order, and adding or removing 1 in the exponent field
+// multiplies a normal number by 2 or 1/2 exactly), leaving the differences
+// and dl + dr on the FP64 pipe.  When dl and dr share a sign both are
+// nonzero and their sum is nonzero; a |dl + dr| below 2^-1021 (no normal
+// halving) gives a zero slope.
 __device__ __forceinline__ double mc_slope(double dl, double dr)
 {
+    constexpr long long ABS = 0x7fffffffffffffffll, ONE_EXP = 1ll << 52;
     const long long bl = __double_as_longlong(dl), br = __double_as_longlong(dr);
-    const long long al = bl & 0x7fffffffffffffffll, ar = br & 0x7fffffffffffffffll;
+    const long long al = bl & ABS, ar = br & ABS;
     const bool same = ((bl ^ br) >= 0) && al != 0 && ar != 0;
-    const double m = __longlong_as_double(min(al, ar));
-    const double twice = m + m;
-    const double half_sum = 0.5 * fabs(dl + dr);
-    const double a = __longlong_as_double(min(__double_as_longlong(twice), __double_as_longlong(half_sum)));
+    const long long m = min(al, ar);
+    const long long twice = m < (0x7fell << 52) ? m + ONE_EXP : m;       // 2 min(|dl|, |dr|)
+    const long long as = __double_as_longlong(dl + dr) & ABS;
+    const long long half = as >= (2ll << 52) ? as - ONE_EXP : 0ll;        // |dl + dr| / 2
+    const double a = __longlong_as_double(min(twice, half));
     return same ? copysign(a, dr) : 0.0;
 }
 
@@ -140,17 +146,26 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     const T rho = HSE ? bg.rho + w[0] : w[0];
     const T pr = HSE ? bg.p + w[NV - 1] : w[NV - 1];
     const T rinv = rcp_t(rho);
+    const T gp = gam * pr;
     T rate[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) rate[q] = T(0);
+    // A_d(w) dw_d / dx_d summed over d, with 1/dx_d folded into the
+    // coefficients: rho: u_n drho + rho du_n; u_e: u_n du_e (+ dp/rho for
+    // e = d); p: u_n dp + gamma p du_n
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        const T un = w[1 + d];
-        rate[0] -= (un * dw[d][0] + rho * dw[d][1 + d]) * inv_dx[d];
+        const T un_dx = w[1 + d] * inv_dx[d];
+        const T rho_dx = rho * inv_dx[d];
+        const T rinv_dx = rinv * inv_dx[d];
+        const T gp_dx = gp * inv_dx[d];
+        rate[0] = fma(-un_dx, dw[d][0], rate[0]);
+        rate[0] = fma(-rho_dx, dw[d][1 + d], rate[0]);
 #pragma unroll
-        for (int e = 0; e < ND; ++e) rate[1 + e] -= un * dw[d][1 + e] * inv_dx[d];
-        rate[1 + d] -= dw[d][NV - 1] * rinv * inv_dx[d];
-        rate[NV - 1] -= (un * dw[d][NV - 1] + gam * pr * dw[d][1 + d]) * inv_dx[d];
+        for (int e = 0; e < ND; ++e) rate[1 + e] = fma(-un_dx, dw[d][1 + e], rate[1 + e]);
+        rate[1 + d] = fma(-rinv_dx, dw[d][NV - 1], rate[1 + d]);
+        rate[NV - 1] = fma(-un_dx, dw[d][NV - 1], rate[NV - 1]);
+        rate[NV - 1] = fma(-gp_dx, dw[d][1 + d], rate[NV - 1]);
     }
     // gravity on the velocities: g rho'/rho - B/rho in HSE mode, g otherwise
     T gsrc[ND];

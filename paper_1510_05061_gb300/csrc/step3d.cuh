@@ -28,6 +28,12 @@
 #define HYDRO_PREFETCH 0
 #endif
 
+// Build option: minimum resident CTAs per SM asked of the FP64 kernels
+// (trades registers for occupancy).
+#ifndef HYDRO_FP64_MIN_CTAS
+#define HYDRO_FP64_MIN_CTAS 1
+#endif
+
 namespace hydro {
 
 template <typename T, bool HSE, int TX, int TY>
@@ -457,7 +463,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 }
 
 template <typename T, bool HSE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1) step3d_kernel(const StepArgs a)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 : 1) : HYDRO_FP64_MIN_CTAS) step3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -486,7 +492,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 
 // own time-control block; the CTA that completes the instance's last item
 // sets that instance's next dt (per-instance CFL).
 template <typename T, bool HSE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 && TX * TY <= 256) ? 2 : 1)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 : 1) : HYDRO_FP64_MIN_CTAS)
 step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
                     int nitems, int parity)
 {
