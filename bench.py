@@ -48,6 +48,8 @@ UNIT = "zone-updates/s"
 FLOPS_PER_ZONE_3D = 542
 FLOPS_PER_ZONE_2D = 321
 
+TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16"}
+
 CONFIGS = {
     # name: (builder, description, precision, hse)
     "rt256-fp64": dict(n=256, precision=inputs.FP64, hse=0,
@@ -72,6 +74,35 @@ CONFIGS = {
                      desc="64 independent 3D periodic Kelvin-Helmholtz boxes, n log-uniform in [32, 192] "
                           "(seed 151005062), FP32; one persistent launch per step, autotuned tiles"),
 }
+
+
+def kernel_source_sha() -> str:
+    """Hash of the CUDA sources: measured traffic is valid only for the
+    kernels it was taken from."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1510_05061_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(f, "rb") as fh:
+                h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(config: str, kernel: str):
+    """DRAM bytes per launch of `kernel` on `config` from the committed ncu
+    table (profiles/traffic.json), or None when absent or stale."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = table.get(config, {}).get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return float(e["bytes_per_launch"])
 
 
 def measured_peaks():
@@ -325,6 +356,7 @@ def run_gpu_batch(args):
     achieved = 2 * 5 * 4 * cells / (per_launch_ms * 1e-3) / 1e9
     items3, items2, grid3, grid2 = b.items()
     b.close()
+    kname = f"step3d_batch_kernel<float, 0, {TILE_NAMES[tune['variant']]}>"
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -336,8 +368,9 @@ def run_gpu_batch(args):
                        "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (cells * 20 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": args.traffic, "peak_kind": peak_kind,
-                         "kernel": "step3d_batch_kernel<float>"},
+                         "frac": achieved / hbm_peak, "peak_kind": peak_kind, "kernel": kname,
+                         "traffic": args.traffic if args.traffic is not None else measured_traffic(args.config, kname),
+                         "algorithmic_bytes": 2 * 5 * 4 * cells},
             "autotune": {k: v for k, v in tune.items() if k != "table"},
             "cpu_baseline": None, "e2e": None,
             "gpu_launches": launches, "clocks": clk.summary(),
@@ -488,21 +521,25 @@ def run_gpu(args):
     achieved_gbs = bytes_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
+    tile = TILE_NAMES.get(tune["variant"] if tune else 0, "32, 8") if prob.ndim == 3 else "32, 8"
+    kname = (f"step3d_kernel<{'double' if itemsize == 8 else 'float'}, {prob.hse_subtract}, {tile}>"
+             if prob.ndim == 3 else f"step2d_kernel<{'double' if itemsize == 8 else 'float'}, 32, 8>")
+    traffic = args.traffic if args.traffic is not None else measured_traffic(args.config, kname)
     if prob.precision == inputs.FP64:
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak_tf = fp64_peak_tflops(sm_mhz)
         ach_tf = flops_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": ach_tf / peak_tf, "traffic": args.traffic,
+                    "frac": ach_tf / peak_tf, "traffic": traffic,
                     "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
-                    "kernel": "step3d_kernel<double>" if prob.ndim == 3 else "step2d_kernel<double>",
+                    "kernel": kname, "algorithmic_bytes": bytes_per_zone * zones_per_launch,
                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                             "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind}}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm_peak, "traffic": args.traffic,
-                    "peak_kind": peak_kind,
-                    "kernel": "step3d_kernel<float>" if prob.ndim == 3 else "step2d_kernel<float>"}
+                    "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                    "peak_kind": peak_kind, "kernel": kname,
+                    "algorithmic_bytes": bytes_per_zone * zones_per_launch}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
