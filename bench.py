@@ -70,6 +70,9 @@ CONFIGS = {
                         "reductions, 150 GB HBM budget, continuous batching"),
     "served-saturation": dict(served=True, rate=500.0,
                               desc="served workload as above with arrivals 10x faster (saturation run)"),
+    "rt256-fp64-slabs4": dict(n=256, precision=inputs.FP64, hse=0, slabs=4,
+                              desc="3D Rayleigh-Taylor 256^3 FP64 cut into 4 z slabs run as virtual ranks "
+                                   "(depth-2 halo exchange + dt max-reduction every step)"),
     "kh-batch": dict(batch=True, count=64, precision=inputs.FP32,
                      desc="64 independent 3D periodic Kelvin-Helmholtz boxes, n log-uniform in [32, 192] "
                           "(seed 151005062), FP32; one persistent launch per step, autotuned tiles"),
@@ -426,8 +429,88 @@ def run_served(args):
     return 0
 
 
+# ------------------------------------------------------ z-slab decomposition
+def run_gpu_slabs(args):
+    """The decomposed step (R slabs on one GPU) timed beside the undivided
+    step on the same grid; both start from the same state."""
+    import torch
+
+    from paper_1510_05061_gb300 import autotune
+    from paper_1510_05061_gb300 import build as hbuild
+    from paper_1510_05061_gb300 import hydro
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    hbuild.build()
+    hydro.load()
+    prob, W, c = build_workload(args.config)
+    R = c["slabs"]
+    stream = torch.cuda.current_stream()
+    sim = hydro.Simulation(prob, W, stream=stream)
+    tune = None
+    if not args.no_tune:
+        tune = autotune.tune_simulation(sim, use_cache=not args.retune)
+        tune = {k: v for k, v in tune.items() if k != "table"}
+        sim.close()
+        sim = hydro.Simulation(prob, W, stream=stream)
+        sim.configure(tune["variant"], tune["zchunk"])
+    slabs = hydro.Slabs(prob, W, R, stream=stream)
+    if tune is not None:
+        slabs.configure(tune["variant"], tune["zchunk"])
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return max_over_ranks(world, e0.elapsed_time(e1))
+
+    whole_ms = timed(lambda: sim.step())
+    n0 = slabs.launches()
+    with ClockSampler(local) as clk:
+        el_ms = timed(lambda: slabs.step(1))
+    launches = slabs.launches() - n0 - args.warmup * (R + 1)
+    same = bool(np.array_equal(sim.get_state(), slabs.get_state()))
+    sim.close()
+    slabs.close()
+    N = prob.ncell
+    value = world * N * args.steps / (el_ms * 1e-3)
+    peaks, peak_kind = measured_peaks()
+    peak_tf = fp64_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    ach_tf = FLOPS_PER_ZONE_3D * N / (el_ms / args.steps * 1e-3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": c["desc"], "grid": list(prob.n), "slabs": R,
+                       "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (N * 40 / 1e6),
+                       "parallelism": "virtual ranks on one GPU"},
+            "undivided_ms_per_step": whole_ms / args.steps,
+            "decomposition_overhead": el_ms / whole_ms - 1.0,
+            "bitwise_equal_to_undivided": same,
+            "autotune": tune,
+            "roofline": {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": ach_tf / peak_tf, "traffic": None,
+                         "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                         "kernel": "step3d_kernel<double, 0, ...> over all slabs (whole step time)"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # -------------------------------------------------------------- GPU arm
 def run_gpu(args):
+    if CONFIGS[args.config].get("slabs"):
+        return run_gpu_slabs(args)
     if CONFIGS[args.config].get("batch"):
         return run_gpu_batch(args)
     if CONFIGS[args.config].get("served"):

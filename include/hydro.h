@@ -261,6 +261,59 @@ int hydro_batch_destroy(hydro_batch *b);
 int hydro_totals_noalloc(const hydro_problem *prob, const void *U, const double *bg,
                          void *stream, double *out);
 
+/* ---- Domain decomposition into z slabs (virtual ranks) ----------------
+   The paper's codes split the domain across nodes and exchange boundary
+   data with their neighbours every step, with one global reduction for the
+   time step (introduction, "Capabilities needed").  These calls cut a 3D
+   problem into R slabs along z (rank r holds planes [z0, z0 + nz) with
+   R's extra planes given to the lowest ranks) and advance all of them on
+   the current device: every step is (1) the halo exchange, two planes of
+   every variable from each neighbour (periodic z wraps; a physical z end
+   keeps its boundary condition), (2) the step kernel on every slab, (3) a
+   max-reduction of the slabs' CFL signal speeds giving every slab the same
+   next dt.  The result is bitwise the undivided solve's.  On a machine with
+   one GPU per rank, (1) becomes point-to-point copies and (3) an allreduce;
+   hydro_slabs_exchange_plan gives the copy list for either.  Requires
+   ndim == 3 and n[2] / R >= 2.  No time control: every step takes the CFL
+   dt (t_end is not clamped). */
+typedef struct hydro_slabs hydro_slabs;
+
+/* Planes of rank `rank`: first global plane and count. */
+int hydro_slab_extent(const hydro_problem *global, int nranks, int rank, int *z0, int *nz);
+/* Bytes of one state buffer of rank `rank` (its nz + 4 planes, halos
+   included) and of its workspace; 0 when the decomposition is invalid. */
+size_t hydro_slab_state_bytes(const hydro_problem *global, int nranks, int rank);
+size_t hydro_slab_workspace_bytes(const hydro_problem *global, int nranks, int rank);
+/* The halo copies of one step as (src rank, src first interior plane,
+   dst rank, dst first stored plane: -2 or nz) quadruples into out (up to
+   max_copies; out may be NULL to count).  Each copy moves two planes of
+   every variable.  Returns the number of copies or a negative status. */
+int hydro_slabs_exchange_plan(const hydro_problem *global, int nranks, int *out, int max_copies);
+/* Ua[r], Ub[r], work[r]: device buffers of hydro_slab_state_bytes /
+   hydro_slab_workspace_bytes (256-byte aligned, caller owned, kept until
+   hydro_slabs_destroy).  W0 and bg: the GLOBAL host arrays of hydro_init
+   (each rank reads its own planes).  Synchronises `stream`. */
+int hydro_slabs_init(const hydro_problem *global, int nranks, void *const *Ua, void *const *Ub,
+                     void *const *work, const double *W0, const double *bg, void *stream,
+                     hydro_slabs **out);
+/* Choose the 3D tile shape and z-chunk (0: default) of the slabs' steps. */
+int hydro_slabs_configure(hydro_slabs *s, int variant, int zchunk);
+/* Enqueue nsteps full steps (exchange, R step kernels, dt reduction each).
+   The R step kernels run concurrently on internal streams forked from and
+   joined back into `stream`; everything is ordered on `stream`. */
+int hydro_slabs_step(hydro_slabs *s, long nsteps);
+/* Gather the interior state of all slabs into one GLOBAL host array in
+   hydro_get_state's layout (synchronises). */
+int hydro_slabs_get_state(hydro_slabs *s, void *host_dst);
+/* FP64 total conserved (what = 0) or primitive (1) fields of the whole
+   domain into a GLOBAL host array, as hydro_get_fields (synchronises). */
+int hydro_slabs_get_fields(hydro_slabs *s, int what, double *host_dst);
+/* hydro_reduce over the whole domain (totals summed over slabs in rank
+   order; scalars from rank 0, identical on all ranks). */
+int hydro_slabs_reduce(hydro_slabs *s, int what, double *out);
+long hydro_slabs_launch_count(hydro_slabs *s);
+int hydro_slabs_destroy(hydro_slabs *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,7 +40,7 @@ __global__ void init_convert_kernel(const AuxArgs a, const double *__restrict__ 
             u[NV - 1] -= a.bg[k + 2].p_c / (a.gamma - 1.0);
         }
 #pragma unroll
-        for (int q = 0; q < NV; ++q) U[q * a.N + c] = T(u[q]);
+        for (int q = 0; q < NV; ++q) U[q * a.vstride + c] = T(u[q]);
     }
 }
 
@@ -65,11 +65,11 @@ __device__ __forceinline__ void cell_prims(const AuxArgs &a, const T *U, long lo
     for (int d = 0; d < 3; ++d) v[d] = T(0);
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        const T m = U[(1 + d) * a.N + c];
+        const T m = U[(1 + d) * a.vstride + c];
         v[d] = m * rinv;
         m2 += m * m;
     }
-    p = bgp + (gam - T(1)) * (U[(NV - 1) * a.N + c] - T(0.5) * m2 * rinv);
+    p = bgp + (gam - T(1)) * (U[(NV - 1) * a.vstride + c] - T(0.5) * m2 * rinv);
 }
 
 template <typename T, int ND, bool HSE>
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(AUX_THREADS) totals_kernel(const AuxArgs a)
         }
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            double v = double(U[q * a.N + c]);
+            double v = double(U[q * a.vstride + c]);
             if (q == 0) v += bgr;
             if (q == NV - 1) v += bge;
             acc[q] += v;
@@ -183,7 +183,7 @@ __global__ void fields_kernel(const AuxArgs a, double *__restrict__ out, long lo
             }
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                double v = double(U[q * a.N + c]);
+                double v = double(U[q * a.vstride + c]);
                 if (q == 0) v += bgr;
                 if (q == NV - 1) v += bge;
                 out[q * m + i] = v;
@@ -201,11 +201,11 @@ __global__ void fields_kernel(const AuxArgs a, double *__restrict__ out, long lo
             out[i] = rho;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                const double mv = double(U[(1 + d) * a.N + c]);
+                const double mv = double(U[(1 + d) * a.vstride + c]);
                 out[(1 + d) * m + i] = mv / rho;
                 m2 += mv * mv;
             }
-            out[(NV - 1) * m + i] = bgp + (a.gamma - 1.0) * (double(U[(NV - 1) * a.N + c]) - 0.5 * m2 / rho);
+            out[(NV - 1) * m + i] = bgp + (a.gamma - 1.0) * (double(U[(NV - 1) * a.vstride + c]) - 0.5 * m2 / rho);
         }
     }
 }
@@ -225,7 +225,7 @@ __global__ void math_kernel(int which, const double *__restrict__ x, const doubl
 template <typename T>
 __global__ void poke_kernel(const AuxArgs a, int var, long long cell, double v)
 {
-    state<T>(a)[var * a.N + cell] = T(v);
+    state<T>(a)[var * a.vstride + cell] = T(v);
 }
 
 int grid_for(long long m)

@@ -106,6 +106,7 @@ AuxArgs aux_for(const InstInfo &I, void *U)
     a.ndim = I.prob.ndim;
     for (int d = 0; d < 3; ++d) { a.n[d] = I.prob.n[d]; a.inv_dx[d] = I.inv_dx[d]; }
     a.N = I.N;
+    a.vstride = I.N;
     a.plane = I.plane;
     a.gamma = I.prob.gamma;
     a.cfl = I.prob.cfl;

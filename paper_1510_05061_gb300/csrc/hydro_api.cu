@@ -122,6 +122,7 @@ AuxArgs aux_args(const hydro_sim *s, void *U)
     a.ndim = s->prob.ndim;
     for (int d = 0; d < 3; ++d) { a.n[d] = s->prob.n[d]; a.inv_dx[d] = s->inv_dx[d]; }
     a.N = s->N;
+    a.vstride = s->N;
     a.plane = s->plane;
     a.gamma = s->prob.gamma;
     a.cfl = s->prob.cfl;

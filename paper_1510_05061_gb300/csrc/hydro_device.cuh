@@ -20,11 +20,17 @@ namespace hydro {
 
 // Interior source index of coordinate g along an axis of n cells (n >= 2),
 // for g in [-2, n+1]; flip is set for a mirror image (reflecting boundary).
+// On a halo side (slab decomposition, z only) g in [-2, -1] or [n, n+1] is
+// returned as is: those planes are stored in the buffer.
 // Coordinates further out (cells of a ragged tile beyond the domain, whose
 // results are never stored) are clamped into range.
+template <bool HALO = false>
 __device__ __forceinline__ int map_index(int g, int n, int bclo, int bchi, bool &flip)
 {
     flip = false;
+    // a halo side (z only): the two planes beyond the slab are stored next to it
+    if constexpr (HALO)
+        if ((g < 0 && bclo == BC_HALO) || (g >= n && bchi == BC_HALO)) return g;
     if (g < 0) {
         if (bclo == BC_PERIODIC) g += n;
         else if (bclo == BC_REFLECT) { g = -1 - g; flip = true; }

@@ -6,7 +6,8 @@
 
 namespace hydro {
 
-enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2 };
+enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2,
+       BC_HALO = 3 };   // z only, internal: planes -2, -1 and nz, nz+1 are stored (slab decomposition)
 
 // Device-resident time control; one per handle, at the start of the
 // workspace.  Written only by the last CTA of a step (or of the dt kernel),

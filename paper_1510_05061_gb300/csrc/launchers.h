@@ -51,9 +51,10 @@ cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp3
 
 // Auxiliary kernels (aux.cu).  fp32 selects the stored precision.
 struct AuxArgs {
-    void *U;              // stored state
+    void *U;              // stored state (interior plane 0 of variable 0)
     int ndim, n[3];
-    long long N, plane;
+    long long N, plane;   // cells, cells per plane
+    long long vstride;    // distance between variable planes (N, or more with stored halos)
     double gamma, cfl, inv_dx[3], cell_volume;
     Ctrl *ctrl;
     double *partial;      // per-CTA partials (max_ctas * 5 doubles)

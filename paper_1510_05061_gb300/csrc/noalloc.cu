@@ -118,6 +118,7 @@ extern "C" int hydro_totals_noalloc(const hydro_problem *prob, const void *U, co
     a.ndim = prob->ndim;
     for (int d = 0; d < 3; ++d) { a.n[d] = prob->n[d]; a.inv_dx[d] = 1.0 / dx[d]; }
     a.N = N;
+    a.vstride = N;
     a.plane = plane;
     a.gamma = prob->gamma;
     a.cfl = prob->cfl;

@@ -122,7 +122,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     T raw[NLOAD][NV];
     auto fetch = [&](int pz) {
         bool fz;
-        const int gz = map_index(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
+        const int gz = map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
             const int i = tid + j * NT;
@@ -131,7 +131,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                 bool fx, fy;
                 const int gx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
                 const int gy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
-                const size_t c = (size_t)gz * a.plane + (size_t)gy * nx + gx;
+                // gz is -2 or -1 below a halo side: signed plane offset
+                const long long c = (long long)gz * a.plane + (long long)gy * nx + gx;
                 raw[j][0] = U[c];
                 const T m0 = U[c + vs], m1 = U[c + 2 * vs], m2 = U[c + 3 * vs];
                 raw[j][1] = fx ? -m0 : m0;

@@ -50,7 +50,9 @@ EXPORTS = (
     "hydro_batch_create", "hydro_batch_add", "hydro_batch_remove", "hydro_batch_set_graph",
     "hydro_batch_configure", "hydro_batch_variant_shape", "hydro_batch_step", "hydro_batch_reduce",
     "hydro_batch_get_fields", "hydro_batch_get_state", "hydro_batch_current", "hydro_batch_launch_count", "hydro_batch_items",
-    "hydro_batch_destroy",
+    "hydro_batch_destroy", "hydro_slab_extent", "hydro_slab_state_bytes", "hydro_slab_workspace_bytes",
+    "hydro_slabs_exchange_plan", "hydro_slabs_init", "hydro_slabs_configure", "hydro_slabs_step",
+    "hydro_slabs_get_state", "hydro_slabs_get_fields", "hydro_slabs_reduce", "hydro_slabs_launch_count", "hydro_slabs_destroy",
 )
 
 
@@ -159,6 +161,31 @@ def load(path: str = LIB_PATH):
     L.hydro_batch_destroy.argtypes = [vp]
     L.hydro_totals_noalloc.restype = C.c_int
     L.hydro_totals_noalloc.argtypes = [P, vp, D, vp, D]
+    IP = C.POINTER(C.c_int)
+    L.hydro_slab_extent.restype = C.c_int
+    L.hydro_slab_extent.argtypes = [P, C.c_int, C.c_int, IP, IP]
+    L.hydro_slab_state_bytes.restype = C.c_size_t
+    L.hydro_slab_state_bytes.argtypes = [P, C.c_int, C.c_int]
+    L.hydro_slab_workspace_bytes.restype = C.c_size_t
+    L.hydro_slab_workspace_bytes.argtypes = [P, C.c_int, C.c_int]
+    L.hydro_slabs_exchange_plan.restype = C.c_int
+    L.hydro_slabs_exchange_plan.argtypes = [P, C.c_int, IP, C.c_int]
+    L.hydro_slabs_init.restype = C.c_int
+    L.hydro_slabs_init.argtypes = [P, C.c_int, PP, PP, PP, D, D, vp, C.POINTER(vp)]
+    L.hydro_slabs_configure.restype = C.c_int
+    L.hydro_slabs_configure.argtypes = [vp, C.c_int, C.c_int]
+    L.hydro_slabs_step.restype = C.c_int
+    L.hydro_slabs_step.argtypes = [vp, C.c_long]
+    L.hydro_slabs_get_state.restype = C.c_int
+    L.hydro_slabs_get_state.argtypes = [vp, vp]
+    L.hydro_slabs_get_fields.restype = C.c_int
+    L.hydro_slabs_get_fields.argtypes = [vp, C.c_int, D]
+    L.hydro_slabs_reduce.restype = C.c_int
+    L.hydro_slabs_reduce.argtypes = [vp, C.c_int, D]
+    L.hydro_slabs_launch_count.restype = C.c_long
+    L.hydro_slabs_launch_count.argtypes = [vp]
+    L.hydro_slabs_destroy.restype = C.c_int
+    L.hydro_slabs_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -526,6 +553,132 @@ class Batch:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             load().hydro_batch_destroy(self.h)
+            self.h = None
+        self._bufs = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------- z-slab decomposition
+
+def hydro_slab_extent(prob: hydro_problem, nranks: int, rank: int):
+    """(first global plane, plane count) of slab `rank`."""
+    z0, nz = C.c_int(), C.c_int()
+    _check(load().hydro_slab_extent(C.byref(prob), int(nranks), int(rank), C.byref(z0), C.byref(nz)),
+           "hydro_slab_extent")
+    return z0.value, nz.value
+
+
+def hydro_slabs_exchange_plan(prob: hydro_problem, nranks: int):
+    """Halo copies of one step: list of (src rank, src first interior plane,
+    dst rank, dst first stored plane), each moving two planes of every
+    variable.  Host-only: needs no GPU."""
+    L = load()
+    n = L.hydro_slabs_exchange_plan(C.byref(prob), int(nranks), None, 0)
+    if n < 0:
+        raise HydroError(n, "hydro_slabs_exchange_plan")
+    out = (C.c_int * (4 * max(n, 1)))()
+    m = L.hydro_slabs_exchange_plan(C.byref(prob), int(nranks), out, n)
+    if m < 0:
+        raise HydroError(m, "hydro_slabs_exchange_plan")
+    return [tuple(out[4 * i:4 * i + 4]) for i in range(m)]
+
+
+class Slabs:
+    """One 3D problem cut into `nranks` z slabs advanced as virtual ranks on
+    the current device: per step a depth-2 halo exchange, the step kernel on
+    every slab and a max-reduction of the CFL signal speed.  Results are
+    bitwise those of ``Simulation`` on the undivided grid."""
+
+    def __init__(self, prob: "inputs.Problem", W0: np.ndarray, nranks: int, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhydro needs a CUDA device")
+        self.prob, self.nranks = prob, int(nranks)
+        self.cp = make_problem(prob)
+        L = load()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._bufs = []
+
+        def alloc(n):
+            if n == 0:
+                raise HydroError(HYDRO_ERR_INVALID_ARG, "slab decomposition")
+            t = torch.empty(n + 256, dtype=torch.uint8, device=dev)
+            self._bufs.append(t)
+            return (t.data_ptr() + 255) // 256 * 256
+
+        ua, ub, wk = [], [], []
+        for r in range(self.nranks):
+            sb = L.hydro_slab_state_bytes(C.byref(self.cp), self.nranks, r)
+            wb = L.hydro_slab_workspace_bytes(C.byref(self.cp), self.nranks, r)
+            ua.append(alloc(sb))
+            ub.append(alloc(sb))
+            wk.append(alloc(wb))
+        self._W0 = np.ascontiguousarray(W0, dtype=np.float64)
+        if self._W0.shape != tuple(prob.shape):
+            raise ValueError(f"W0 shape {self._W0.shape} != {prob.shape}")
+        self._bg = background_tables(prob)
+        VP = C.c_void_p * self.nranks
+        h = C.c_void_p()
+        _check(L.hydro_slabs_init(C.byref(self.cp), self.nranks, VP(*ua), VP(*ub), VP(*wk),
+                                  _dptr(self._W0), _dptr(self._bg), C.c_void_p(self.stream.cuda_stream),
+                                  C.byref(h)), "hydro_slabs_init")
+        self.h = h
+
+    def configure(self, variant: int, zchunk: int = 0):
+        _check(load().hydro_slabs_configure(self.h, int(variant), int(zchunk)), "hydro_slabs_configure")
+
+    def step(self, n: int = 1):
+        _check(load().hydro_slabs_step(self.h, int(n)), "hydro_slabs_step")
+
+    def reduce(self, what: int) -> np.ndarray:
+        out = np.zeros(self.prob.nvar, dtype=np.float64)
+        _check(load().hydro_slabs_reduce(self.h, int(what), _dptr(out)), "hydro_slabs_reduce")
+        return out
+
+    def totals(self) -> np.ndarray:
+        return self.reduce(HYDRO_RED_TOTALS)
+
+    @property
+    def t(self) -> float:
+        return float(self.reduce(HYDRO_RED_TIME)[0])
+
+    @property
+    def dt(self) -> float:
+        return float(self.reduce(HYDRO_RED_DT)[0])
+
+    @property
+    def nstep(self) -> int:
+        return int(self.reduce(HYDRO_RED_STEP)[0])
+
+    def get_state(self) -> np.ndarray:
+        dt = np.float32 if self.prob.precision == inputs.FP32 else np.float64
+        out = np.empty(self.prob.shape, dtype=dt)
+        _check(load().hydro_slabs_get_state(self.h, C.c_void_p(out.ctypes.data)), "hydro_slabs_get_state")
+        return out
+
+    def conserved(self) -> np.ndarray:
+        out = np.empty(self.prob.shape, dtype=np.float64)
+        _check(load().hydro_slabs_get_fields(self.h, 0, _dptr(out)), "hydro_slabs_get_fields")
+        return out
+
+    def primitive(self) -> np.ndarray:
+        out = np.empty(self.prob.shape, dtype=np.float64)
+        _check(load().hydro_slabs_get_fields(self.h, 1, _dptr(out)), "hydro_slabs_get_fields")
+        return out
+
+    def launches(self) -> int:
+        return load().hydro_slabs_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().hydro_slabs_destroy(self.h)
             self.h = None
         self._bufs = []
 
