@@ -54,6 +54,7 @@ class _Params(C.Structure):
         ("hse", C.c_int),
         ("bg_rho_c", C.c_void_p), ("bg_p_c", C.c_void_p),
         ("bg_rho_f", C.c_void_p), ("bg_p_f", C.c_void_p),
+        ("scheme", C.c_int),
     ]
 
 
@@ -129,6 +130,7 @@ class Oracle:
         p.gamma = float(prob.gamma)
         p.cfl = float(prob.cfl)
         p.hse = int(prob.hse_subtract)
+        p.scheme = int(getattr(prob, "scheme", 0))
         if prob.hse_subtract:
             for name in ("bg_rho_c", "bg_p_c", "bg_rho_f", "bg_p_f"):
                 arr = np.ascontiguousarray(getattr(prob, name), dtype=np.float64)

@@ -27,6 +27,14 @@
  *     reflecting = mirror with the normal momentum negated); at a reflecting
  *     wall the far-side face state is the mirror of the near side's.
  *
+ * Second integrator (scheme = 1): the method of lines with the two-stage
+ * strong-stability-preserving Runge-Kutta method of Shu and Osher (1988),
+ *   U1 = U^n + dt L(U^n),   U^{n+1} = (U^n + U1 + dt L(U1)) / 2,
+ * where L is the same spatial operator without the half-step predictor: face
+ * states W -/+ dW/2 from the MC slopes (same positivity fallback), HLLC,
+ * flux divergence, momentum source g rho of the stage state and the same
+ * mass-flux energy source.  dt is taken from U^n.
+ *
  * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
  * may load this file's library.  It shares no code with the CUDA path.
  *
@@ -56,6 +64,7 @@
 #define MAXV 5
 
 enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2 };
+enum { SCHEME_HANCOCK = 0, SCHEME_SSPRK2 = 1 };
 enum { OK = 0, ERR_ARG = -1, ERR_OOM = -2, ERR_NONPHYSICAL = -4 };
 
 typedef struct {
@@ -70,6 +79,7 @@ typedef struct {
        k in [-2, nz + 2), face table index f + 2 for the face z_lo + f dz,
        f in [-2, nz + 2]. */
     const double *bg_rho_c, *bg_p_c, *bg_rho_f, *bg_p_f;
+    int scheme;     /* SCHEME_HANCOCK or SCHEME_SSPRK2 */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -112,6 +122,7 @@ static int check_params(const orc_params *p)
         if (!(p->hi[d] > p->lo[d])) return ERR_ARG;
     }
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return ERR_ARG;
+    if (p->scheme != SCHEME_HANCOCK && p->scheme != SCHEME_SSPRK2) return ERR_ARG;
     if (p->hse) {
         if (p->ndim != 3) return ERR_ARG;
         if (!p->bg_rho_c || !p->bg_p_c || !p->bg_rho_f || !p->bg_p_f) return ERR_ARG;
@@ -352,7 +363,11 @@ static int work_alloc(const orc_params *p, work_t *w)
 /* padded z-plane kk -> interior plane index k (may be outside [0, nz)) */
 static inline int zplane(const grid_t *g, int kk) { return kk - g->ng[2]; }
 
-static int step_with(const orc_params *p, work_t *wk, double *U, double dt)
+/* One update U <- U + dt * (flux divergence + sources).  With predictor = 1
+   it is the MUSCL-Hancock step; with predictor = 0 it is one forward-Euler
+   stage U + dt L(U) of the method of lines (face states W -/+ dW/2, gravity
+   on the momentum from the stage density). */
+static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int predictor)
 {
     const grid_t *g = &wk->g;
     const int nd = g->ndim, nv = g->nvar;
@@ -438,7 +453,10 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt)
                 }
                 /* gravity: du/dt = g (rho' / rho); rho'/rho = 1 in plain mode */
                 for (int d = 0; d < nd; ++d) dwdt[1 + d] += p->grav[d] * (w[0] / rho);
-                for (int q = 0; q < nv; ++q) wh[q] = w[q] + hdt * dwdt[q];
+                if (predictor)
+                    for (int q = 0; q < nv; ++q) wh[q] = w[q] + hdt * dwdt[q];
+                else
+                    for (int q = 0; q < nv; ++q) wh[q] = w[q];
 
                 double wf[3][2][MAXV];
                 int bad = 0;
@@ -458,8 +476,10 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt)
                     /* positivity fallback: zero every slope of this cell */
                     double w0[MAXV];
                     for (int q = 0; q < nv; ++q) w0[q] = w[q];
-                    for (int d = 0; d < nd; ++d) w0[1 + d] += hdt * p->grav[d] * (w[0] / rho);
-                    if (p->hse) w0[3] -= hdt * B / rho;
+                    if (predictor) {
+                        for (int d = 0; d < nd; ++d) w0[1 + d] += hdt * p->grav[d] * (w[0] / rho);
+                        if (p->hse) w0[3] -= hdt * B / rho;
+                    }
                     for (int d = 0; d < nd; ++d)
                         for (int s = 0; s < 2; ++s)
                             for (int q = 0; q < nv; ++q) wf[d][s][q] = w0[q];
@@ -519,8 +539,9 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt)
     }
 
     /* 6. conservative update, density first, then momentum with
-       the time-centred density in the gravity source, then energy with the
-       mass fluxes through the two faces */
+       the time-centred density in the gravity source (MUSCL-Hancock) or the
+       stage density (method of lines), then energy with the mass fluxes
+       through the two faces */
     int bad_total = 0;
     #pragma omp parallel for collapse(2) schedule(static) reduction(| : bad_total)
     for (int k = 0; k < g->n[2]; ++k)
@@ -547,7 +568,8 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt)
                 double rho_new = rho_old + dt * du[0];
                 U[0 * N + o] = rho_new;
                 for (int d = 0; d < nd; ++d) {
-                    double src = p->grav[d] * 0.5 * (rho_old + rho_new);
+                    double src = predictor ? p->grav[d] * 0.5 * (rho_old + rho_new)
+                                           : p->grav[d] * rho_old;
                     if (p->hse && d == 2) src -= B;
                     U[(1 + d) * N + o] += dt * (du[1 + d] + src);
                 }
@@ -585,13 +607,44 @@ int orc_max_threads(void)
 #endif
 }
 
+/* One full step of the problem's integrator with the given dt. */
+static int full_step(const orc_params *p, work_t *wk, double *U, double *U0, double dt)
+{
+    if (p->scheme == SCHEME_HANCOCK) return step_with(p, wk, U, dt, 1);
+    /* SSP-RK2: U0 keeps U^n; U becomes U1, then U1 + dt L(U1), then the
+       average with U^n */
+    const long n = (long)wk->g.nvar * wk->g.n[0] * wk->g.n[1] * wk->g.n[2];
+    memcpy(U0, U, sizeof(double) * n);
+    int rc1 = step_with(p, wk, U, dt, 0);   /* checks U1 */
+    step_with(p, wk, U, dt, 0);             /* U1 + dt L(U1): only its average is a state */
+    for (long i = 0; i < n; ++i) U[i] = 0.5 * (U0[i] + U[i]);
+    /* admissibility of U^{n+1} */
+    const grid_t *g = &wk->g;
+    const long N = (long)g->n[0] * g->n[1] * g->n[2];
+    int bad = 0;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                long c = ((long)k * g->n[1] + j) * g->n[0] + i;
+                double u[MAXV], w[MAXV];
+                for (int q = 0; q < g->nvar; ++q) u[q] = U[q * N + c];
+                cons_to_prim(g->ndim, p->gamma, bg_rho_centre(p, k), u, w);
+                double rt = bg_rho_centre(p, k) + w[0], pt = bg_p_centre(p, k) + w[g->ndim + 1];
+                if (!(rt > 0.0) || !(pt > 0.0) || !isfinite(rt) || !isfinite(pt)) bad = 1;
+            }
+    return rc1 ? rc1 : bad ? ERR_NONPHYSICAL : OK;
+}
+
 int orc_step(const orc_params *p, double *U, double dt)
 {
     int rc = check_params(p);
     if (rc) return rc;
     work_t wk;
     if (work_alloc(p, &wk)) return ERR_OOM;
-    rc = step_with(p, &wk, U, dt);
+    double *U0 = (double *)malloc(sizeof(double) * wk.g.nvar * wk.g.n[0] * wk.g.n[1] * wk.g.n[2]);
+    if (!U0) { work_free(&wk); return ERR_OOM; }
+    rc = full_step(p, &wk, U, U0, dt);
+    free(U0);
     work_free(&wk);
     return rc;
 }
@@ -607,6 +660,8 @@ int orc_run(const orc_params *p, double *U, double t0, double t_end, long max_st
     if (rc) return rc;
     work_t wk;
     if (work_alloc(p, &wk)) return ERR_OOM;
+    double *U0 = (double *)malloc(sizeof(double) * wk.g.nvar * wk.g.n[0] * wk.g.n[1] * wk.g.n[2]);
+    if (!U0) { work_free(&wk); return ERR_OOM; }
     double t = t0, dt_last = 0.0;
     long s = 0;
     while (s < max_steps && t < t_end) {
@@ -614,13 +669,14 @@ int orc_run(const orc_params *p, double *U, double t0, double t_end, long max_st
         double tn;
         if (dt >= t_end - t) { dt = t_end - t; tn = t_end; }
         else tn = t + dt;
-        rc = step_with(p, &wk, U, dt);
+        rc = full_step(p, &wk, U, U0, dt);
         if (dts) dts[s] = dt;
         t = tn;
         dt_last = dt;
         ++s;
         if (rc) break;
     }
+    free(U0);
     work_free(&wk);
     if (t_out) *t_out = t;
     if (steps_out) *steps_out = s;

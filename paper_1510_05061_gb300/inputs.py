@@ -41,6 +41,9 @@ BC_REFLECT = 2
 FP64 = 0
 FP32 = 1
 
+HANCOCK = 0   # single-stage unsplit MUSCL-Hancock
+SSPRK2 = 1    # two-stage SSP Runge-Kutta method of lines
+
 _MASK = (1 << 64) - 1
 _GOLDEN = 0x9E3779B97F4A7C15
 
@@ -59,6 +62,8 @@ class Problem:
     of planes k = -2 .. nz+1 (length nz + 4, entry k + 2) and ``bg_rho_f`` /
     ``bg_p_f`` at the faces z_lo + f dz, f = -2 .. nz+2 (length nz + 5, entry
     f + 2).  Ghost planes need the background outside the domain.
+    ``scheme`` selects the time integrator: HANCOCK (single-stage
+    MUSCL-Hancock) or SSPRK2 (two-stage method of lines).
     """
 
     ndim: int
@@ -77,6 +82,7 @@ class Problem:
     bg_p_c: Optional[np.ndarray] = None
     bg_rho_f: Optional[np.ndarray] = None
     bg_p_f: Optional[np.ndarray] = None
+    scheme: int = 0
 
     @property
     def nvar(self) -> int:
