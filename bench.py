@@ -47,6 +47,12 @@ UNIT = "zone-updates/s"
 # 2D = 10 + 40 + 50 + 32 + 2 x 64 + 42 + 19 = 321.
 FLOPS_PER_ZONE_3D = 542
 FLOPS_PER_ZONE_2D = 321
+# SSP-RK2 method of lines, per step: two stages without the half step
+# (3D 13 + 75 + 60 + 216 + 70 = 434, 2D 10 + 40 + 32 + 128 + 42 = 252), the
+# stage average (2 per variable) and one CFL speed.  Bytes per zone-update:
+# stage 1 reads U and writes U1, stage 2 reads U1 and U and writes U^{n+1}.
+FLOPS_PER_ZONE_3D_RK2 = 2 * 434 + 10 + 25
+FLOPS_PER_ZONE_2D_RK2 = 2 * 252 + 8 + 19
 
 TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16"}
 
@@ -70,6 +76,12 @@ CONFIGS = {
                         "reductions, 150 GB HBM budget, continuous batching"),
     "served-saturation": dict(served=True, rate=500.0,
                               desc="served workload as above with arrivals 10x faster (saturation run)"),
+    "rt256-fp64-rk2": dict(n=256, precision=inputs.FP64, hse=0, scheme=inputs.SSPRK2,
+                           desc="3D Rayleigh-Taylor 256^3 FP64 with the SSP-RK2 method-of-lines integrator "
+                                "(two stage kernels per step)"),
+    "rt512-fp32-rk2": dict(n=512, precision=inputs.FP32, hse=1, scheme=inputs.SSPRK2,
+                           desc="3D Rayleigh-Taylor 512^3 FP32 bulk with background subtraction, SSP-RK2 "
+                                "method of lines"),
     "rt256-fp64-slabs4": dict(n=256, precision=inputs.FP64, hse=0, slabs=4,
                               desc="3D Rayleigh-Taylor 256^3 FP64 cut into 4 z slabs run as virtual ranks "
                                    "(depth-2 halo exchange + dt max-reduction every step)"),
@@ -227,6 +239,7 @@ def build_workload(cfg):
         prob, W = inputs.kelvin_helmholtz(c["n"], ndim=2, U=1.0, ratio=2.0, precision=c["precision"])
     else:
         prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
+    prob = prob.replace(scheme=c.get("scheme", inputs.HANCOCK))
     return prob, W, c
 
 
@@ -598,15 +611,22 @@ def run_gpu(args):
 
     # ---- roofline of the step kernel
     peaks, peak_kind = measured_peaks()
-    bytes_per_zone = 2 * prob.nvar * itemsize
+    rk2 = prob.scheme == inputs.SSPRK2
+    # per step: one kernel (MUSCL-Hancock) or the two stage kernels (SSP-RK2)
+    bytes_per_zone = (5 if rk2 else 2) * prob.nvar * itemsize
     zones_per_launch = N
-    flops_per_zone = FLOPS_PER_ZONE_3D if prob.ndim == 3 else FLOPS_PER_ZONE_2D
+    if rk2:
+        flops_per_zone = FLOPS_PER_ZONE_3D_RK2 if prob.ndim == 3 else FLOPS_PER_ZONE_2D_RK2
+    else:
+        flops_per_zone = FLOPS_PER_ZONE_3D if prob.ndim == 3 else FLOPS_PER_ZONE_2D
     achieved_gbs = bytes_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
     tile = TILE_NAMES.get(tune["variant"] if tune else 0, "32, 8") if prob.ndim == 3 else "32, 8"
     kname = (f"step3d_kernel<{'double' if itemsize == 8 else 'float'}, {prob.hse_subtract}, {tile}>"
              if prob.ndim == 3 else f"step2d_kernel<{'double' if itemsize == 8 else 'float'}, 32, 8>")
+    if rk2:
+        kname = kname.replace(">", ", stage 1> + ") + kname.replace(">", ", stage 2> (one step)")
     traffic = args.traffic if args.traffic is not None else measured_traffic(args.config, kname)
     if prob.precision == inputs.FP64:
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))

@@ -64,6 +64,14 @@ typedef enum {
 
 enum { HYDRO_BC_OUTFLOW = 0, HYDRO_BC_PERIODIC = 1, HYDRO_BC_REFLECT = 2 };
 enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1 /* FP32 state and update, FP64 dt, time and totals */ };
+/* Time integrators.  HANCOCK: single-stage unsplit MUSCL-Hancock (Toro, 3rd
+   ed., sec. 14.4), one kernel per step.  SSPRK2: method of lines with the
+   two-stage SSP Runge-Kutta method of Shu and Osher (1988), U1 = U + dt L(U),
+   U^{n+1} = (U + U1 + dt L(U1)) / 2, L the same PLM-MC/HLLC operator
+   without the half-step predictor; two kernels per step and one more state
+   in the workspace.  SSPRK2 is available through hydro_init only (not in
+   batches or slab decompositions). */
+enum { HYDRO_SCHEME_HANCOCK = 0, HYDRO_SCHEME_SSPRK2 = 1 };
 enum {
     HYDRO_RED_TOTALS = 1,    /* out[nvar]: sum over cells of (rho, m_d, E) * cell volume, FP64, fixed order */
     HYDRO_RED_DT = 2,        /* out[1]: CFL dt of the current state */
@@ -86,6 +94,7 @@ typedef struct {
     double grav[3];
     int precision;       /* HYDRO_FP64 or HYDRO_FP32 */
     int hse_subtract;
+    int scheme;          /* HYDRO_SCHEME_HANCOCK (0) or HYDRO_SCHEME_SSPRK2 */
 } hydro_problem;
 
 typedef struct hydro_sim hydro_sim;

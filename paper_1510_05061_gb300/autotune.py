@@ -116,7 +116,9 @@ def sim_signature(sim) -> str:
 
     p = sim.prob
     prec = "fp32" if p.precision == inputs.FP32 else "fp64"
-    return f"{torch.cuda.get_device_name()}|single|{prec}|hse{p.hse_subtract}|n={p.n[0]}x{p.n[1]}x{p.n[2]}"
+    scheme = "rk2" if getattr(p, "scheme", 0) == inputs.SSPRK2 else "hancock"
+    return (f"{torch.cuda.get_device_name()}|single|{prec}|hse{p.hse_subtract}|{scheme}"
+            f"|n={p.n[0]}x{p.n[1]}x{p.n[2]}")
 
 
 def time_sim_steps(sim, steps: int) -> float:

@@ -277,6 +277,7 @@ int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, 
     if (!prob || !Ua || !Ub || !inst_work || !W0 || Ua == Ub) return HYDRO_ERR_INVALID_ARG;
     if (!aligned(Ua) || !aligned(Ub) || !aligned(inst_work)) return HYDRO_ERR_INVALID_ARG;
     if (hydro_state_bytes(prob) == 0 || prob->precision != b->precision) return HYDRO_ERR_INVALID_ARG;
+    if (prob->scheme != HYDRO_SCHEME_HANCOCK) return HYDRO_ERR_INVALID_ARG;   // batches step MUSCL-Hancock
     if (prob->hse_subtract && !bg) return HYDRO_ERR_INVALID_ARG;
     if (prob->ndim == 3 && b->hse3 >= 0 && prob->hse_subtract != b->hse3) {
         // one launch serves all 3D instances: one mode per batch
@@ -463,7 +464,9 @@ size_t hydro_batch_workspace_bytes(const hydro_problem *probs, int count)
     long long cap3 = 0, cap2 = 0;
     size_t inst = 0;
     for (int i = 0; i < count; ++i) {
-        if (hydro_state_bytes(&probs[i]) == 0 || probs[i].precision != probs[0].precision) return 0;
+        if (hydro_state_bytes(&probs[i]) == 0 || probs[i].precision != probs[0].precision ||
+            probs[i].scheme != HYDRO_SCHEME_HANCOCK)
+            return 0;
         (probs[i].ndim == 3 ? cap3 : cap2) += (long long)max_items_of(probs[i]);
         inst += inst_layout(probs[i]).total;
     }

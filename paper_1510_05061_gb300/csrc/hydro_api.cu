@@ -29,6 +29,7 @@ struct hydro_sim {
     double *partial;
     PlaneBG *bg;
     PlaneBGT<float> *bgf;
+    void *stage;             // first Runge-Kutta stage state (SSP-RK2), in the workspace
     cudaStream_t stream;
     double dx[3], inv_dx[3], cell_volume;
     int tiles_x, tiles_y;
@@ -70,6 +71,7 @@ int check_problem(const hydro_problem *p)
         return HYDRO_ERR_INVALID_ARG;
     if (p->precision != HYDRO_FP64 && p->precision != HYDRO_FP32) return HYDRO_ERR_INVALID_ARG;
     if (p->hse_subtract != 0 && p->hse_subtract != 1) return HYDRO_ERR_INVALID_ARG;
+    if (p->scheme != HYDRO_SCHEME_HANCOCK && p->scheme != HYDRO_SCHEME_SSPRK2) return HYDRO_ERR_INVALID_ARG;
     if (p->hse_subtract && (p->ndim != 3 || p->grav[0] != 0.0 || p->grav[1] != 0.0))
         return HYDRO_ERR_INVALID_ARG;
     // 32-bit plane and cell indexing inside a plane; 64-bit across planes
@@ -108,6 +110,10 @@ WorkLayout layout(const hydro_problem *p)
     off = align_up(off + (p->hse_subtract ? sizeof(PlaneBG) * (size_t)(p->n[2] + 5) : 0));
     L.bgf = off;
     off = align_up(off + (p->hse_subtract ? sizeof(PlaneBGT<float>) * (size_t)(p->n[2] + 5) : 0));
+    // the first Runge-Kutta stage's state (SSP-RK2 only)
+    L.stage = off;
+    if (p->scheme == HYDRO_SCHEME_SSPRK2)
+        off = align_up(off + (size_t)N * (p->ndim + 2) * (p->precision == HYDRO_FP32 ? 4 : 8));
     L.red = off;
     L.total = off;
     return L;
@@ -172,26 +178,45 @@ StepArgs step_args(const hydro_sim *s, double t_end)
     if (s->prob.hse_subtract)
         a.bgT = s->prob.precision == HYDRO_FP32 ? static_cast<const void *>(s->bgf)
                                                 : static_cast<const void *>(s->bg);
+    a.U0 = nullptr;
     a.zchunk = s->zchunk;
     a.tiles_x = s->tiles_x;
     return a;
+}
+
+cudaError_t launch_kernel(hydro_sim *s, const StepArgs &a, int stage)
+{
+    const bool fp32 = s->prob.precision == HYDRO_FP32;
+    const bool hse = s->prob.hse_subtract != 0;
+    s->launches += 1;
+    if (s->prob.ndim == 2) return launch_step2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32, stage);
+    const dim3 grid(s->tiles_x * s->tiles_y, (s->prob.n[2] + s->zchunk - 1) / s->zchunk);
+    if (stage == STAGE_HANCOCK)
+        return fp32 ? launch_step3d_f32(s->variant, a, grid, s->stream, hse)
+                    : launch_step3d_f64(s->variant, a, grid, s->stream, hse);
+    return fp32 ? launch_stage3d_f32(stage, s->variant, a, grid, s->stream, hse)
+                : launch_stage3d_f64(stage, s->variant, a, grid, s->stream, hse);
 }
 
 int launch_step(hydro_sim *s, double t_end)
 {
     StepArgs a = step_args(s, t_end);
     cudaError_t e;
-    const bool fp32 = s->prob.precision == HYDRO_FP32;
-    if (s->prob.ndim == 2) {
-        dim3 grid(s->tiles_x * s->tiles_y, 1);
-        e = launch_step2d(a, grid, s->stream, fp32);
+    if (s->prob.scheme == HYDRO_SCHEME_SSPRK2) {
+        // U1 = U + dt L(U) into the stage buffer, then
+        // U^{n+1} = (U + U1 + dt L(U1)) / 2 into the other state buffer
+        StepArgs a1 = a;
+        a1.Unew = s->stage;
+        e = launch_kernel(s, a1, STAGE_RK1);
+        if (e == cudaSuccess) {
+            StepArgs a2 = a;
+            a2.U = s->stage;
+            a2.U0 = s->buf[s->cur];
+            e = launch_kernel(s, a2, STAGE_RK2);
+        }
     } else {
-        const int nch = (s->prob.n[2] + s->zchunk - 1) / s->zchunk;
-        dim3 grid(s->tiles_x * s->tiles_y, nch);
-        e = fp32 ? launch_step3d_f32(s->variant, a, grid, s->stream, s->prob.hse_subtract != 0)
-                 : launch_step3d_f64(s->variant, a, grid, s->stream, s->prob.hse_subtract != 0);
+        e = launch_kernel(s, a, STAGE_HANCOCK);
     }
-    s->launches += 1;
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
     s->cur = 1 - s->cur;
     return HYDRO_OK;
@@ -279,6 +304,7 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
     s->partial = reinterpret_cast<double *>(s->work + s->lay.partial);
     s->bg = reinterpret_cast<PlaneBG *>(s->work + s->lay.bg);
     s->bgf = reinterpret_cast<PlaneBGT<float> *>(s->work + s->lay.bgf);
+    s->stage = s->work + s->lay.stage;
     s->stream = static_cast<cudaStream_t>(stream);
     s->cell_volume = 1.0;
     for (int d = 0; d < 3; ++d) {

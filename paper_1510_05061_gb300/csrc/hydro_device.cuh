@@ -213,6 +213,32 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     return !ok;
 }
 
+// Face states of the method of lines (no predictor): w -/+ dw_d / 2, with
+// the same positivity fallback as the half step (every slope of the cell
+// zeroed when a face density or pressure would not be positive).
+template <typename T, int ND, bool HSE>
+__device__ __forceinline__ void mol_faces(const T (&w)[ND + 2], T (&dw)[ND][ND + 2], const CellBG<T> &bg)
+{
+    constexpr int NV = ND + 2;
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        T rb_lo = bg.rho, rb_hi = bg.rho, pb_lo = bg.p, pb_hi = bg.p;
+        if (HSE && d == 2) { rb_lo = bg.rho_lo; rb_hi = bg.rho_hi; pb_lo = bg.p_lo; pb_hi = bg.p_hi; }
+        const T r_lo = rb_lo + (w[0] - T(0.5) * dw[d][0]);
+        const T r_hi = rb_hi + (w[0] + T(0.5) * dw[d][0]);
+        const T p_lo = pb_lo + (w[NV - 1] - T(0.5) * dw[d][NV - 1]);
+        const T p_hi = pb_hi + (w[NV - 1] + T(0.5) * dw[d][NV - 1]);
+        ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
+    }
+    if (!ok) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) dw[d][q] = T(0);
+    }
+}
+
 // HLLC flux along axis D (Toro, 3rd ed., sec. 10.4-10.6) with Davis wave
 // speeds S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R).
 // wl, wr hold (rho', u, p') and (rb, pb) the background at the face; in plain

@@ -55,6 +55,7 @@ struct StepArgs {
     Ctrl *ctrl;
     double *partial;    // per-CTA max signal speed
     const void *bgT;    // hse tables in the step's precision (nullptr in plain mode)
+    const void *U0;     // second Runge-Kutta stage: U^n, read at the cell's own position
     int zchunk;         // planes per CTA (3D)
     int tiles_x;        // tiles along x
 };
@@ -76,8 +77,12 @@ struct BatchInst {
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WorkLayout {
-    size_t ctrl, partial, bg, bgf, red, total;
+    size_t ctrl, partial, bg, bgf, stage, red, total;   // stage: first Runge-Kutta stage state
     int max_ctas;
 };
+
+// Kernel stage of a step: the MUSCL-Hancock step, or the first / second
+// stage of the SSP-RK2 method of lines.
+enum { STAGE_HANCOCK = 0, STAGE_RK1 = 1, STAGE_RK2 = 2 };
 
 }  // namespace hydro

@@ -48,6 +48,7 @@ bool extent(const hydro_problem *g, int R, int r, int *z0, int *nz)
 bool valid_global(const hydro_problem *g, int R)
 {
     if (!g || g->ndim != 3 || R <= 0 || hydro_state_bytes(g) == 0) return false;
+    if (g->scheme != HYDRO_SCHEME_HANCOCK) return false;   // slabs step MUSCL-Hancock
     return g->n[2] / R >= 2;   // every slab supplies two halo planes
 }
 

@@ -1,14 +1,15 @@
-// step2d.cu -- FP64 and FP32 instantiations of the fused 2D step.
+// step2d.cu -- FP64 and FP32 instantiations of the fused 2D step and of
+// the two Runge-Kutta stages.
 #include "launchers.h"
 #include "step2d.cuh"
 
 namespace hydro {
 
-template <typename T>
+template <typename T, int ST>
 static cudaError_t launch2d(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
     constexpr int TX = STEP2D_TX, TY = STEP2D_TY;
-    auto k = step2d_kernel<T, TX, TY>;
+    auto k = step2d_kernel<T, TX, TY, ST>;
     constexpr size_t smem = Step2DSmem<T, TX, TY>::bytes;
     static bool configured = false;
     if (!configured) {
@@ -20,9 +21,20 @@ static cudaError_t launch2d(const StepArgs &a, dim3 grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32)
+template <int ST>
+static cudaError_t launch2d_p(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32)
 {
-    return fp32 ? launch2d<float>(a, grid, s) : launch2d<double>(a, grid, s);
+    return fp32 ? launch2d<float, ST>(a, grid, s) : launch2d<double, ST>(a, grid, s);
+}
+
+cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32, int stage)
+{
+    switch (stage) {
+    case STAGE_HANCOCK: return launch2d_p<STAGE_HANCOCK>(a, grid, s, fp32);
+    case STAGE_RK1: return launch2d_p<STAGE_RK1>(a, grid, s, fp32);
+    case STAGE_RK2: return launch2d_p<STAGE_RK2>(a, grid, s, fp32);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace hydro

@@ -29,7 +29,7 @@ struct Step2DSmem {
 };
 
 template <typename T, int TX, int TY>
-__device__ __forceinline__ void step2d_copy(const StepArgs &a, int tile)
+__device__ __forceinline__ void step2d_copy(const StepArgs &a, int tile, const void *src)
 {
     constexpr int NV = 4;
     const int nx = a.n[0], ny = a.n[1];
@@ -38,12 +38,13 @@ __device__ __forceinline__ void step2d_copy(const StepArgs &a, int tile)
     if (gx < nx && gy < ny)
         for (int q = 0; q < NV; ++q) {
             const size_t c = (size_t)q * a.vstride + (size_t)gy * nx + gx;
-            static_cast<T *>(a.Unew)[c] = static_cast<const T *>(a.U)[c];
+            static_cast<T *>(a.Unew)[c] = static_cast<const T *>(src)[c];
         }
 }
 
-// One CTA's share of a 2D step: tile `tile` (row-major over tiles_x).
-template <typename T, int TX, int TY>
+// One CTA's share of a 2D step: tile `tile` (row-major over tiles_x).  ST
+// selects the MUSCL-Hancock step or a Runge-Kutta stage as in step3d_body.
+template <typename T, int TX, int TY, int ST = STAGE_HANCOCK>
 __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
@@ -60,6 +61,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = (tile / a.tiles_x) * TY;
     const T *__restrict__ U = static_cast<const T *>(a.U);
+    const T *__restrict__ U0 = static_cast<const T *>(a.U0);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
     const long long vs = a.vstride;
     const int gx = x0 + tx, gy = y0 + ty;
@@ -110,7 +112,13 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
             dw[0][q] = mc_slope(c - P(q, hy, hx - 1), P(q, hy, hx + 1) - c);
             dw[1][q] = mc_slope(c - P(q, hy - 1, hx), P(q, hy + 1, hx) - c);
         }
-        hancock<T, ND, false>(w, dw, wh, hdt, inv_dx, gam, grav, nobg);
+        if constexpr (ST == STAGE_HANCOCK) {
+            hancock<T, ND, false>(w, dw, wh, hdt, inv_dx, gam, grav, nobg);
+        } else {
+            mol_faces<T, ND, false>(w, dw, nobg);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) wh[q] = w[q];
+        }
     };
 
     // ---- half step: tile cells, then the cross-shaped ring
@@ -226,10 +234,14 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
         const T r_old = u[0];
         const T r_new = r_old + dt * du[0];
         u[0] = r_new;
-        const T rsum = T(0.5) * (r_old + r_new);
+        const T rsum = ST == STAGE_HANCOCK ? T(0.5) * (r_old + r_new) : r_old;
         u[1] += dt * (du[1] + grav[0] * rsum);
         u[2] += dt * (du[2] + grav[1] * rsum);
         u[3] += dt * (du[3] + msrc);
+        if constexpr (ST == STAGE_RK2) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) u[q] = T(0.5) * (U0[c + q * vs] + u[q]);
+        }
 #pragma unroll
         for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
         const T rinv = rcp_t(u[0]);
@@ -243,7 +255,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     }
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int ST = STAGE_HANCOCK>
 __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
@@ -253,14 +265,19 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     const double t_now = a.ctrl->t;
     const double dt_cfl = a.ctrl->dt_next;
     if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
-        step2d_copy<T, TX, TY>(a, blockIdx.x);
+        if constexpr (ST == STAGE_HANCOCK) step2d_copy<T, TX, TY>(a, blockIdx.x, a.U);
+        if constexpr (ST == STAGE_RK2) step2d_copy<T, TX, TY>(a, blockIdx.x, a.U0);
         return;
     }
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    step2d_body<T, TX, TY>(a, blockIdx.x, dtd, smem_raw, smax, bad);
+    step2d_body<T, TX, TY, ST>(a, blockIdx.x, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
+    if constexpr (ST == STAGE_RK1) {
+        if (bad_cta && threadIdx.x == 0) atomicOr(&a.ctrl->err_new, 1);
+        return;
+    }
     const double m = block_max_t<NT, T>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd,
                     true, &s_last);
@@ -288,7 +305,7 @@ step2d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
         const double t_now = sa.ctrl->t;
         const double dt_cfl = sa.ctrl->dt_next;
         if (t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end) {
-            step2d_copy<T, TX, TY>(sa, w.tile);
+            step2d_copy<T, TX, TY>(sa, w.tile, sa.U);
         } else {
             const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
             T smax;

@@ -54,16 +54,16 @@ struct Step3DSmem {
 };
 
 // Frozen step (time already at t_end, or the handle in its error state):
-// the tile's cells are carried over unchanged.
+// the tile's cells of `src` (U^n) are carried over unchanged.
 template <typename T, int TX, int TY>
-__device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chunk)
+__device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chunk, const void *src)
 {
     constexpr int NV = 5;
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int gx = (tile % a.tiles_x) * TX + tx, gy = (tile / a.tiles_x) * TY + ty;
     const int z0 = chunk * a.zchunk, z1 = min(z0 + a.zchunk, nz);
-    const T *U = static_cast<const T *>(a.U);
+    const T *U = static_cast<const T *>(src);
     T *Un = static_cast<T *>(a.Unew);
     if (gx < nx && gy < ny)
         for (int k = z0; k < z1; ++k)
@@ -77,7 +77,11 @@ __device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chu
 // plane, z planes [chunk*zchunk, min((chunk+1)*zchunk, nz)), time step dtd.
 // On return smax/bad hold this thread's max CFL signal speed and whether one
 // of its new cells failed the admissibility check.
-template <typename T, bool HSE, int TX, int TY>
+// ST selects the update (STAGE_*): the MUSCL-Hancock step; the first
+// Runge-Kutta stage U1 = U + dt L(U); or the second, (U0 + U + dt L(U)) / 2
+// with U = U1 and U0 = U^n.  The stages have no half-step predictor and
+// take the gravity source on the momentum from the stage's own density.
+template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK>
 __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chunk, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
@@ -99,6 +103,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     const int z0 = chunk * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
     const T *__restrict__ U = static_cast<const T *>(a.U);
+    const T *__restrict__ U0 = static_cast<const T *>(a.U0);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
     const long long vs = a.vstride;
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
@@ -175,7 +180,13 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             dw[2][q] = mc_slope(c - P(sm, q, hy, hx), P(sp, q, hy, hx) - c);
         }
         const CellBG<T> bg = cell_bg<T, HSE>(bgT, p);
-        hancock<T, ND, HSE>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
+        if constexpr (ST == STAGE_HANCOCK) {
+            hancock<T, ND, HSE>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
+        } else {
+            mol_faces<T, ND, HSE>(w, dw, bg);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) wh[q] = w[q];
+        }
     };
 
     auto WX = [&](T *base, int q, int cy, int cx) -> T & {   // cx in [-1, TX]
@@ -215,12 +226,16 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         // the plane completed at the end of this iteration is p-1: start its
         // own-cell loads now so that they overlap the half step and fluxes
         const bool fin = p > z0 && own;
-        T ufin[NV];
+        T ufin[NV], u0fin[NV];
         T bgB = T(0), bgR = T(0), bgP = T(0);
         if (fin) {
             const size_t c = (size_t)(p - 1) * a.plane + (size_t)gy * nx + gx;
 #pragma unroll
             for (int q = 0; q < NV; ++q) ufin[q] = U[c + q * vs];
+            if constexpr (ST == STAGE_RK2) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) u0fin[q] = U0[c + q * vs];
+            }
             if constexpr (HSE) {
                 bgB = bgT[p + 1].B;
                 bgR = bgT[p + 1].rho_c;
@@ -424,7 +439,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             const T r_old = u[0];
             const T r_new = r_old + dt * du[0];
             u[0] = r_new;
-            const T rsum = T(0.5) * (r_old + r_new);
+            // gravity on the momentum: time-centred density (MUSCL-Hancock)
+            // or the stage's density (Runge-Kutta stages)
+            const T rsum = ST == STAGE_HANCOCK ? T(0.5) * (r_old + r_new) : r_old;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 T src = grav[d] * rsum;
@@ -432,6 +449,10 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                 u[1 + d] += dt * (du[1 + d] + src);
             }
             u[4] += dt * (du[4] + msrc);
+            if constexpr (ST == STAGE_RK2) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) u[q] = T(0.5) * (u0fin[q] + u[q]);
+            }
 #pragma unroll
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
             // CFL signal speed and admissibility of the new state
@@ -463,7 +484,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
 }
 
-template <typename T, bool HSE, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK>
 __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 : 1) : HYDRO_FP64_MIN_CTAS) step3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
@@ -471,18 +492,28 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 
     __shared__ double red[32];
     __shared__ int s_last;
     const int tile = blockIdx.x, chunk = blockIdx.y;
-    // time control: dt from the device block, clamped to t_end
+    // time control: dt from the device block, clamped to t_end (both
+    // Runge-Kutta stages read the same block: the first stage leaves it
+    // unchanged apart from its error bits)
     const double t_now = a.ctrl->t;
     const double dt_cfl = a.ctrl->dt_next;
     if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
-        step3d_copy<T, TX, TY>(a, tile, chunk);
+        // U^n carried over: by the step, or by the second stage (from U0)
+        if constexpr (ST == STAGE_HANCOCK) step3d_copy<T, TX, TY>(a, tile, chunk, a.U);
+        if constexpr (ST == STAGE_RK2) step3d_copy<T, TX, TY>(a, tile, chunk, a.U0);
         return;
     }
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    step3d_body<T, HSE, TX, TY>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    step3d_body<T, HSE, TX, TY, ST>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
+    if constexpr (ST == STAGE_RK1) {
+        // the intermediate state only raises error bits; dt and time move
+        // at the end of the second stage
+        if (bad_cta && threadIdx.x == 0) atomicOr(&a.ctrl->err_new, 1);
+        return;
+    }
     const double m = block_max_t<NT, T>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd,
                     true, &s_last);
@@ -512,7 +543,7 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
         const double t_now = sa.ctrl->t;
         const double dt_cfl = sa.ctrl->dt_next;
         if (t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end) {
-            step3d_copy<T, TX, TY>(sa, w.tile, w.chunk);
+            step3d_copy<T, TX, TY>(sa, w.tile, w.chunk, sa.U);
         } else {
             const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
             T smax;
