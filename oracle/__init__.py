@@ -54,7 +54,7 @@ class _Params(C.Structure):
         ("hse", C.c_int),
         ("bg_rho_c", C.c_void_p), ("bg_p_c", C.c_void_p),
         ("bg_rho_f", C.c_void_p), ("bg_p_f", C.c_void_p),
-        ("scheme", C.c_int),
+        ("scheme", C.c_int), ("recon", C.c_int),
     ]
 
 
@@ -70,6 +70,8 @@ def lib():
             P = C.POINTER(_Params)
             L.orc_mc_slope.restype = C.c_double
             L.orc_mc_slope.argtypes = [C.c_double, C.c_double]
+            L.orc_ppm_faces.restype = None
+            L.orc_ppm_faces.argtypes = [C.c_double] * 6 + [_D, _D]
             L.orc_hllc.restype = None
             L.orc_hllc.argtypes = [C.c_int, C.c_double, C.c_int, _D, _D, _D]
             L.orc_phys_flux.restype = None
@@ -131,6 +133,7 @@ class Oracle:
         p.cfl = float(prob.cfl)
         p.hse = int(prob.hse_subtract)
         p.scheme = int(getattr(prob, "scheme", 0))
+        p.recon = int(getattr(prob, "recon", 0))
         if prob.hse_subtract:
             for name in ("bg_rho_c", "bg_p_c", "bg_rho_f", "bg_p_f"):
                 arr = np.ascontiguousarray(getattr(prob, name), dtype=np.float64)
@@ -203,6 +206,13 @@ class Oracle:
 
 
 # single-face helpers for unit tests ------------------------------------------
+
+def ppm_faces(am: float, a: float, ap: float, sm: float, s: float, sp: float):
+    """Limited PPM values at the low and high faces of a cell."""
+    lo, hi = C.c_double(), C.c_double()
+    lib().orc_ppm_faces(am, a, ap, sm, s, sp, C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
 
 def mc_slope(dl: float, dr: float) -> float:
     return lib().orc_mc_slope(float(dl), float(dr))

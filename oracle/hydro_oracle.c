@@ -35,6 +35,13 @@
  * flux divergence, momentum source g rho of the stage state and the same
  * mass-flux energy source.  dt is taken from U^n.
  *
+ * Second reconstruction (recon = 1, with scheme = 1 and hse = 0 only): the
+ * piecewise parabolic method of Colella and Woodward (1984) in primitive
+ * variables, used as the method of lines' face states: the interface value
+ * a_{i+1/2} = (a_i + a_{i+1})/2 - (dm_{i+1} - dm_i)/6 from the MC-limited
+ * slopes dm (their eqs. 1.7-1.9 on a uniform grid), then the parabola of
+ * cell i limited to be monotone (their eq. 1.10).  Needs three ghost cells.
+ *
  * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
  * may load this file's library.  It shares no code with the CUDA path.
  *
@@ -61,10 +68,12 @@
 #endif
 
 #define NG 2        /* ghost depth: PLM slope of a face-neighbour */
+#define NG_PPM 3    /* PPM: interface values of a face-neighbour */
 #define MAXV 5
 
 enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2 };
 enum { SCHEME_HANCOCK = 0, SCHEME_SSPRK2 = 1 };
+enum { RECON_PLM = 0, RECON_PPM = 1 };
 enum { OK = 0, ERR_ARG = -1, ERR_OOM = -2, ERR_NONPHYSICAL = -4 };
 
 typedef struct {
@@ -80,6 +89,7 @@ typedef struct {
        f in [-2, nz + 2]. */
     const double *bg_rho_c, *bg_p_c, *bg_rho_f, *bg_p_f;
     int scheme;     /* SCHEME_HANCOCK or SCHEME_SSPRK2 */
+    int recon;      /* RECON_PLM or RECON_PPM */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -100,7 +110,7 @@ static void grid_make(const orc_params *p, grid_t *g)
     g->npad = 1;
     for (int d = 0; d < 3; ++d) {
         g->n[d] = p->n[d];
-        g->ng[d] = d < p->ndim ? NG : 0;
+        g->ng[d] = d < p->ndim ? (p->recon == RECON_PPM ? NG_PPM : NG) : 0;
         g->P[d] = g->n[d] + 2 * g->ng[d];
         g->npad *= g->P[d];
         g->dx[d] = (p->hi[d] - p->lo[d]) / (double)p->n[d];
@@ -123,6 +133,12 @@ static int check_params(const orc_params *p)
     }
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return ERR_ARG;
     if (p->scheme != SCHEME_HANCOCK && p->scheme != SCHEME_SSPRK2) return ERR_ARG;
+    if (p->recon != RECON_PLM && p->recon != RECON_PPM) return ERR_ARG;
+    if (p->recon == RECON_PPM) {
+        if (p->scheme != SCHEME_SSPRK2 || p->hse) return ERR_ARG;
+        for (int d = 0; d < p->ndim; ++d)
+            if (p->n[d] < 3) return ERR_ARG;
+    }
     if (p->hse) {
         if (p->ndim != 3) return ERR_ARG;
         if (!p->bg_rho_c || !p->bg_p_c || !p->bg_rho_f || !p->bg_p_f) return ERR_ARG;
@@ -247,6 +263,38 @@ double orc_mc_slope(double dl, double dr)
     double a = fmin(2.0 * fabs(dl), 2.0 * fabs(dr));
     a = fmin(a, 0.5 * fabs(dl + dr));
     return dr > 0.0 ? a : -a;
+}
+
+/* ------------------------------------------------------------------ */
+/* PPM face values (Colella and Woodward 1984, uniform grid).  am, a, ap:  */
+/* the values of cells i-1, i, i+1; sm, s, sp: their MC-limited slopes.    */
+/* Returns the limited parabola's values at the low and high faces of i.   */
+/* ------------------------------------------------------------------ */
+
+void orc_ppm_faces(double am, double a, double ap, double sm, double s, double sp,
+                   double *lo, double *hi)
+{
+    /* interface values (their eq. 1.9 with the limited slopes of eq. 1.8) */
+    double aL = 0.5 * (am + a) - (s - sm) / 6.0;
+    double aR = 0.5 * (a + ap) - (sp - s) / 6.0;
+    /* monotone parabola (their eq. 1.10) */
+    if ((aR - a) * (a - aL) <= 0.0) {
+        aL = a;
+        aR = a;
+    } else {
+        double da = aR - aL;
+        double a6 = 6.0 * (a - 0.5 * (aL + aR));
+        if (da * a6 > da * da) aL = 3.0 * a - 2.0 * aR;
+        else if (-(da * da) > da * a6) aR = 3.0 * a - 2.0 * aL;
+    }
+    *lo = aL;
+    *hi = aR;
+}
+
+static void ppm_faces(double am, double a, double ap, double sm, double s, double sp,
+                      double *lo, double *hi)
+{
+    orc_ppm_faces(am, a, ap, sm, s, sp, lo, hi);
 }
 
 /* ------------------------------------------------------------------ */
@@ -393,12 +441,15 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
             }
         }
 
-    /* cells that need slopes, predictor and face states: one ring beyond
-       the interior along each active axis */
-    int lo[3], hi[3];
+    /* cells that need slopes: every padded cell with both neighbours along
+       each active axis; cells that need face states: one ring beyond the
+       interior (the same cells for PLM's two ghosts) */
+    int lo[3], hi[3], flo_c[3], fhi_c[3];
     for (int d = 0; d < 3; ++d) {
         lo[d] = g->ng[d] > 0 ? 1 : 0;
         hi[d] = g->ng[d] > 0 ? g->P[d] - 1 : g->P[d];   /* exclusive */
+        flo_c[d] = g->ng[d] > 0 ? g->ng[d] - 1 : 0;
+        fhi_c[d] = g->ng[d] > 0 ? g->ng[d] + g->n[d] + 1 : g->P[d];
     }
 
     /* 3. MC slopes of each primitive along each axis */
@@ -417,18 +468,19 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
             }
 
     /* 4. MUSCL-Hancock half step in primitive variables, all axes
-       at once, then face states W +- dW/2 with the per-cell fallback */
+       at once, then face states W +- dW/2 (or PPM's) with the per-cell
+       fallback */
     const double hdt = 0.5 * dt;
     #pragma omp parallel for collapse(2) schedule(static)
-    for (int kk = lo[2]; kk < hi[2]; ++kk)
-        for (int j = lo[1]; j < hi[1]; ++j) {
+    for (int kk = flo_c[2]; kk < fhi_c[2]; ++kk)
+        for (int j = flo_c[1]; j < fhi_c[1]; ++j) {
             int k = zplane(g, kk);
             double rho_bg = bg_rho_centre(p, k), p_bg = bg_p_centre(p, k);
             /* background slopes and discrete imbalance across the cell (z) */
             double drho_bg = bg_rho_face(p, k + 1) - bg_rho_face(p, k);
             double dp_bg = bg_p_face(p, k + 1) - bg_p_face(p, k);
             double B = p->hse ? dp_bg / g->dx[2] - rho_bg * p->grav[2] : 0.0;
-            for (int i = lo[0]; i < hi[0]; ++i) {
+            for (int i = flo_c[0]; i < fhi_c[0]; ++i) {
                 long c = pidx(g, i, j, kk);
                 double w[MAXV], dw[3][MAXV], wh[MAXV];
                 for (int q = 0; q < nv; ++q) w[q] = wk->W[q * np + c];
@@ -460,10 +512,20 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
 
                 double wf[3][2][MAXV];
                 int bad = 0;
+                if (p->recon == RECON_PPM) {
+                    for (int d = 0; d < nd; ++d)
+                        for (int q = 0; q < nv; ++q) {
+                            const double *Wq = wk->W + q * np;
+                            const double *Dq = wk->dW + (d * nv + q) * np;
+                            ppm_faces(Wq[c - st[d]], Wq[c], Wq[c + st[d]], Dq[c - st[d]], Dq[c],
+                                      Dq[c + st[d]], &wf[d][0][q], &wf[d][1][q]);
+                        }
+                }
                 for (int d = 0; d < nd; ++d)
                     for (int s = 0; s < 2; ++s) {
                         double sgn = s == 0 ? -0.5 : 0.5;
-                        for (int q = 0; q < nv; ++q) wf[d][s][q] = wh[q] + sgn * dw[d][q];
+                        if (p->recon == RECON_PLM)
+                            for (int q = 0; q < nv; ++q) wf[d][s][q] = wh[q] + sgn * dw[d][q];
                         /* totals at this face for the positivity test */
                         double rb = rho_bg, pb = p_bg;
                         if (p->hse && d == 2) {

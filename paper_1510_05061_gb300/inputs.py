@@ -44,6 +44,9 @@ FP32 = 1
 HANCOCK = 0   # single-stage unsplit MUSCL-Hancock
 SSPRK2 = 1    # two-stage SSP Runge-Kutta method of lines
 
+PLM = 0       # piecewise linear reconstruction, MC limiter
+PPM = 1       # piecewise parabolic reconstruction (SSPRK2, no hse)
+
 _MASK = (1 << 64) - 1
 _GOLDEN = 0x9E3779B97F4A7C15
 
@@ -63,7 +66,8 @@ class Problem:
     ``bg_p_f`` at the faces z_lo + f dz, f = -2 .. nz+2 (length nz + 5, entry
     f + 2).  Ghost planes need the background outside the domain.
     ``scheme`` selects the time integrator: HANCOCK (single-stage
-    MUSCL-Hancock) or SSPRK2 (two-stage method of lines).
+    MUSCL-Hancock) or SSPRK2 (two-stage method of lines); ``recon`` the
+    reconstruction: PLM or PPM (PPM with SSPRK2 and no background only).
     """
 
     ndim: int
@@ -83,6 +87,7 @@ class Problem:
     bg_rho_f: Optional[np.ndarray] = None
     bg_p_f: Optional[np.ndarray] = None
     scheme: int = 0
+    recon: int = 0
 
     @property
     def nvar(self) -> int:
