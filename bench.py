@@ -120,6 +120,49 @@ def measured_traffic(config: str, kernel: str):
     return float(e["bytes_per_launch"])
 
 
+def record_traffic(config: str, csv_path: str) -> int:
+    """Read an ncu CSV (--csv --log-file) of this benchmark taken with
+    --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,
+    store each kernel's mean DRAM bytes per launch for `config` in
+    profiles/traffic.json (with the current source hash) and print the launch
+    list (launches, device time, share, traffic) as a markdown table."""
+    import csv
+    import re
+
+    per = {}
+    with open(csv_path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        name = re.sub(r"^void\s+", "", row["Kernel Name"])
+        name = re.sub(r"\(.*\)$", "", name).strip()
+        name = re.sub(r"^(\w+::|\(anonymous namespace\)::|<?unnamed>::)+", "", name)
+        d = per.setdefault(name, {})
+        d.setdefault(row["ID"], {})[row["Metric Name"]] = float(row["Metric Value"].replace(",", ""))
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            table = json.load(fh)
+    except (OSError, ValueError):
+        table = {}
+    sha = kernel_source_sha()
+    rows = []
+    total_ns = 0.0
+    for name, launches in per.items():
+        ns = sum(m.get("gpu__time_duration.sum", 0.0) for m in launches.values())
+        byts = [m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0) for m in launches.values()]
+        rows.append((name, len(launches), ns, sum(byts) / len(byts)))
+        total_ns += ns
+        table.setdefault(config, {})[name] = {"bytes_per_launch": sum(byts) / len(byts),
+                                              "launches": len(launches), "source_sha": sha}
+    with open(path, "w") as fh:
+        json.dump(table, fh, indent=1, sort_keys=True)
+    print("| kernel | launches | device time (ms) | share | DRAM bytes per launch |")
+    print("|---|---:|---:|---:|---:|")
+    for name, n, ns, b in sorted(rows, key=lambda r: -r[2]):
+        print(f"| `{name}` | {n} | {ns / 1e6:.3f} | {ns / total_ns:.1%} | {b / 1e9:.3f} GB |")
+    return 0
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -623,11 +666,16 @@ def run_gpu(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
     tile = TILE_NAMES.get(tune["variant"] if tune else 0, "32, 8") if prob.ndim == 3 else "32, 8"
-    kname = (f"step3d_kernel<{'double' if itemsize == 8 else 'float'}, {prob.hse_subtract}, {tile}>"
-             if prob.ndim == 3 else f"step2d_kernel<{'double' if itemsize == 8 else 'float'}, 32, 8>")
-    if rk2:
-        kname = kname.replace(">", ", stage 1> + ") + kname.replace(">", ", stage 2> (one step)")
-    traffic = args.traffic if args.traffic is not None else measured_traffic(args.config, kname)
+    tname = "double" if itemsize == 8 else "float"
+    stages = (1, 2) if rk2 else (0,)
+    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}>" if prob.ndim == 3
+               else f"step2d_kernel<{tname}, 32, 8, {st}>") for st in stages]
+    kname = " + ".join(knames)
+    # DRAM bytes of one step: the sum over its kernels (null if any is missing or stale)
+    traffic = args.traffic
+    if traffic is None:
+        per = [measured_traffic(args.config, k) for k in knames]
+        traffic = sum(per) if all(v is not None for v in per) else None
     if prob.precision == inputs.FP64:
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak_tf = fp64_peak_tflops(sm_mhz)
@@ -730,7 +778,11 @@ def main():
                     help="FP32 vs FP64 Rayleigh-Taylor density error at t_end (no JSON bench line)")
     ap.add_argument("--precision-n", type=int, default=512)
     ap.add_argument("--t-end", type=float, default=0.5)
+    ap.add_argument("--record-traffic", metavar="NCU_CSV", default=None,
+                    help="store DRAM bytes per launch from an ncu CSV of --config into profiles/traffic.json")
     args = ap.parse_args()
+    if args.record_traffic:
+        return record_traffic(args.config, args.record_traffic)
     if args.precision_report:
         return run_precision_report(args)
     if args.warmup < 3:
