@@ -21,11 +21,15 @@
 
 #include "hydro_device.cuh"
 
-// Build option: keep the next plane's global loads in flight in registers
-// (FP32 only).  Off by default: measured on GB300 it raises register
-// pressure under the two-CTA bound and costs more than it hides.
-#ifndef HYDRO_PREFETCH
-#define HYDRO_PREFETCH 0
+// Build option: stage the next plane of the FP64 step with asynchronous
+// global->shared copies (cp.async) issued one plane ahead, so that its loads
+// are in flight while the current plane is computed without holding them in
+// registers.  0 keeps the synchronous loads (load, then convert).  Measured
+// on GB300: +1.4 % for FP64 (one CTA per SM); no gain for FP32, whose second
+// resident CTA already hides the load latency, so FP32 always loads
+// synchronously and keeps the shared memory.
+#ifndef HYDRO_ASYNC_STAGING
+#define HYDRO_ASYNC_STAGING 1
 #endif
 
 // Build option: minimum resident CTAs per SM asked of the FP64 kernels
@@ -49,9 +53,25 @@ struct Step3DSmem {
     static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;   // [NV][TY+2][TX]
     static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
     static constexpr size_t fy = (size_t)NV * (TY + 1) * TX;   // [NV][TY+1][TX]
-    static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy;
+    // conserved values of the next two planes as copied from HBM
+    static constexpr bool async = HYDRO_ASYNC_STAGING != 0 && sizeof(T) == 8;
+    static constexpr size_t raw = async ? 2ull * NV * HX * HY : 0;   // [2][NV][HY*HX]
+    static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy + raw;
     static constexpr size_t bytes = elems * sizeof(T);
 };
+
+// Asynchronous 4- or 8-byte global->shared copy (cp.async, cached in L1 and
+// L2) and the completion of all of this thread's copies.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem_dst, const T *gmem_src)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Frozen step (time already at t_end, or the handle in its error state):
 // the tile's cells of `src` (U^n) are carried over unchanged.
@@ -86,15 +106,14 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
-    // FP32 keeps the next plane's loads in flight; FP64 is bound by its
-    // arithmetic pipe and has no registers to spare for them
-    constexpr bool PREFETCH = HYDRO_PREFETCH && sizeof(T) == 4;
     using S = Step3DSmem<T, HSE, TX, TY>;
+    constexpr bool ASYNC = S::async;
     constexpr int HX = S::HX, HY = S::HY;
     T *prim = reinterpret_cast<T *>(smem_raw);
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
     T *fxs = wyh + S::wy, *fys = fxs + S::fx;
+    T *rawbuf = fys + S::fy;
 
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
@@ -119,50 +138,77 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     };
 
     // ---- stage plane pz (may be a ghost plane) into its ring slot, in two
-    // halves: fetch() issues the global loads (boundary conditions applied
-    // by index mapping, mirrored momenta negated) into registers, store()
-    // converts them to primitives in shared memory.  With PREFETCH the fetch
-    // of plane p+2 is in flight while plane p is computed.
+    // halves: fetch() starts the global loads of the haloed plane (boundary
+    // conditions applied by index mapping), store() converts them to
+    // primitives in shared memory, negating mirrored momenta.  With ASYNC
+    // the loads are cp.async copies into a two-plane shared buffer, issued
+    // one plane ahead; each thread converts exactly the elements it copied,
+    // so its own wait_group suffices.  The x-y mapping of a thread's
+    // elements is the same on every plane and is computed once.
     constexpr int NLOAD = (HX * HY + NT - 1) / NT;
-    T raw[NLOAD][NV];
+    constexpr int HXY = HX * HY;
+    int xyoff[NLOAD];         // mapped in-plane offset of each element
+    unsigned flips = 0;       // bit 2j: x mirror, bit 2j+1: y mirror
+#pragma unroll
+    for (int j = 0; j < NLOAD; ++j) {
+        const int i = tid + j * NT;
+        const int hx = i % HX, hy = i / HX;
+        bool fx, fy;
+        const int gxm = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
+        const int gym = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
+        xyoff[j] = gym * nx + gxm;
+        flips |= (fx ? 1u : 0u) << (2 * j);
+        flips |= (fy ? 1u : 0u) << (2 * j + 1);
+    }
+    T raw[ASYNC ? 1 : NLOAD][NV];
     auto fetch = [&](int pz) {
         bool fz;
         const int gz = map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
+        // gz is -2 or -1 below a halo side: signed plane offset
+        const T *Up = U + (long long)gz * a.plane;
+        T *rb = rawbuf + (size_t)((pz + 4) & 1) * (NV * HXY);
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
             const int i = tid + j * NT;
-            if (i < HX * HY) {
-                const int hx = i % HX, hy = i / HX;
-                bool fx, fy;
-                const int gx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
-                const int gy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
-                // gz is -2 or -1 below a halo side: signed plane offset
-                const long long c = (long long)gz * a.plane + (long long)gy * nx + gx;
-                raw[j][0] = U[c];
-                const T m0 = U[c + vs], m1 = U[c + 2 * vs], m2 = U[c + 3 * vs];
-                raw[j][1] = fx ? -m0 : m0;
-                raw[j][2] = fy ? -m1 : m1;
-                raw[j][3] = fz ? -m2 : m2;
-                raw[j][4] = U[c + 4 * vs];
+            if (i < HXY) {
+                const T *src = Up + xyoff[j];
+                if constexpr (ASYNC) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) cp_async_elem(rb + q * HXY + i, src + q * vs);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) raw[ASYNC ? 0 : j][q] = src[q * vs];
+                }
             }
         }
+        if constexpr (ASYNC) cp_async_commit();
     };
     auto store = [&](int pz) {
         const int slot = (pz + 3) % 3;
         const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
+        bool fz;
+        map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
+        const T *rb = rawbuf + (size_t)((pz + 4) & 1) * (NV * HXY);
+        if constexpr (ASYNC) cp_async_wait_all();
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
             const int i = tid + j * NT;
-            if (i < HX * HY) {
+            if (i < HXY) {
                 const int hx = i % HX, hy = i / HX;
-                const T r = raw[j][0], m0 = raw[j][1], m1 = raw[j][2], m2 = raw[j][3];
+                T v[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) v[q] = ASYNC ? rb[q * HXY + i] : raw[ASYNC ? 0 : j][q];
+                const T r = v[0];
+                const T m0 = (flips >> (2 * j)) & 1u ? -v[1] : v[1];
+                const T m1 = (flips >> (2 * j + 1)) & 1u ? -v[2] : v[2];
+                const T m2 = fz ? -v[3] : v[3];
                 const T rho = HSE ? rho_bg + r : r;
                 const T rinv = rcp_t(rho);
                 P(slot, 0, hy, hx) = r;
                 P(slot, 1, hy, hx) = m0 * rinv;
                 P(slot, 2, hy, hx) = m1 * rinv;
                 P(slot, 3, hy, hx) = m2 * rinv;
-                P(slot, 4, hy, hx) = (gam - T(1)) * (raw[j][4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+                P(slot, 4, hy, hx) = (gam - T(1)) * (v[4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
             }
         }
     };
@@ -212,9 +258,14 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     store(z0 - 2);
     fetch(z0 - 1);
     store(z0 - 1);
-    if constexpr (PREFETCH) fetch(z0);
+    if constexpr (ASYNC) {
+        __syncthreads();
+        fetch(z0);
+    }
     for (int p = z0 - 1; p <= z1; ++p) {
-        if constexpr (PREFETCH) {
+        if constexpr (ASYNC) {
+            // plane p+1 was requested one iteration ago; request p+2 into the
+            // buffer plane p used (converted before the last barrier)
             store(p + 1);
             if (p + 2 <= z1 + 1) fetch(p + 2);
         } else {
