@@ -53,6 +53,11 @@ FLOPS_PER_ZONE_2D = 321
 # stage 1 reads U and writes U1, stage 2 reads U1 and U and writes U^{n+1}.
 FLOPS_PER_ZONE_3D_RK2 = 2 * 434 + 10 + 25
 FLOPS_PER_ZONE_2D_RK2 = 2 * 252 + 8 + 19
+# PPM face states instead of W -/+ dW/2, per variable and axis: the interface
+# value (5) and the monotone-parabola limiter (14) on top of the MC slope:
+# 3D stage 13 + 75 + 15 x 19 + 216 + 70 = 659, 2D 10 + 40 + 8 x 19 + 128 + 42 = 372.
+FLOPS_PER_ZONE_3D_PPM = 2 * 659 + 10 + 25
+FLOPS_PER_ZONE_2D_PPM = 2 * 372 + 8 + 19
 
 TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16"}
 
@@ -82,6 +87,10 @@ CONFIGS = {
     "rt512-fp32-rk2": dict(n=512, precision=inputs.FP32, hse=1, scheme=inputs.SSPRK2,
                            desc="3D Rayleigh-Taylor 512^3 FP32 bulk with background subtraction, SSP-RK2 "
                                 "method of lines"),
+    "rt256-fp64-ppm": dict(n=256, precision=inputs.FP64, hse=0, scheme=inputs.SSPRK2, recon=inputs.PPM,
+                           desc="3D Rayleigh-Taylor 256^3 FP64, SSP-RK2 method of lines with PPM face states"),
+    "rt512-fp32-ppm": dict(n=512, precision=inputs.FP32, hse=0, scheme=inputs.SSPRK2, recon=inputs.PPM,
+                           desc="3D Rayleigh-Taylor 512^3 FP32 (FP64 dt and reductions), SSP-RK2 with PPM"),
     "rt256-fp64-slabs4": dict(n=256, precision=inputs.FP64, hse=0, slabs=4,
                               desc="3D Rayleigh-Taylor 256^3 FP64 cut into 4 z slabs run as virtual ranks "
                                    "(depth-2 halo exchange + dt max-reduction every step)"),
@@ -282,7 +291,7 @@ def build_workload(cfg):
         prob, W = inputs.kelvin_helmholtz(c["n"], ndim=2, U=1.0, ratio=2.0, precision=c["precision"])
     else:
         prob, W = inputs.rayleigh_taylor(c["n"], precision=c["precision"], hse_subtract=c["hse"])
-    prob = prob.replace(scheme=c.get("scheme", inputs.HANCOCK))
+    prob = prob.replace(scheme=c.get("scheme", inputs.HANCOCK), recon=c.get("recon", inputs.PLM))
     return prob, W, c
 
 
@@ -658,7 +667,9 @@ def run_gpu(args):
     # per step: one kernel (MUSCL-Hancock) or the two stage kernels (SSP-RK2)
     bytes_per_zone = (5 if rk2 else 2) * prob.nvar * itemsize
     zones_per_launch = N
-    if rk2:
+    if rk2 and prob.recon == inputs.PPM:
+        flops_per_zone = FLOPS_PER_ZONE_3D_PPM if prob.ndim == 3 else FLOPS_PER_ZONE_2D_PPM
+    elif rk2:
         flops_per_zone = FLOPS_PER_ZONE_3D_RK2 if prob.ndim == 3 else FLOPS_PER_ZONE_2D_RK2
     else:
         flops_per_zone = FLOPS_PER_ZONE_3D if prob.ndim == 3 else FLOPS_PER_ZONE_2D
@@ -668,8 +679,9 @@ def run_gpu(args):
     tile = TILE_NAMES.get(tune["variant"] if tune else 0, "32, 8") if prob.ndim == 3 else "32, 8"
     tname = "double" if itemsize == 8 else "float"
     stages = (1, 2) if rk2 else (0,)
-    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}>" if prob.ndim == 3
-               else f"step2d_kernel<{tname}, 32, 8, {st}>") for st in stages]
+    rc = f", {prob.recon}" if prob.recon else ""
+    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}{rc}>" if prob.ndim == 3
+               else f"step2d_kernel<{tname}, 32, 8, {st}{rc}>") for st in stages]
     kname = " + ".join(knames)
     # DRAM bytes of one step: the sum over its kernels (null if any is missing or stale)
     traffic = args.traffic

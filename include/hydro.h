@@ -72,6 +72,11 @@ enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1 /* FP32 state and update, FP64 dt, time an
    in the workspace.  SSPRK2 is available through hydro_init only (not in
    batches or slab decompositions). */
 enum { HYDRO_SCHEME_HANCOCK = 0, HYDRO_SCHEME_SSPRK2 = 1 };
+/* Face-state reconstruction.  PLM: MC-limited piecewise linear (van Leer
+   1977).  PPM: the piecewise parabolic method (Colella and Woodward 1984):
+   interface values from the MC-limited slopes, parabola limited to be
+   monotone; needs HYDRO_SCHEME_SSPRK2, hse_subtract = 0 and n[d] >= 3. */
+enum { HYDRO_RECON_PLM = 0, HYDRO_RECON_PPM = 1 };
 enum {
     HYDRO_RED_TOTALS = 1,    /* out[nvar]: sum over cells of (rho, m_d, E) * cell volume, FP64, fixed order */
     HYDRO_RED_DT = 2,        /* out[1]: CFL dt of the current state */
@@ -95,6 +100,7 @@ typedef struct {
     int precision;       /* HYDRO_FP64 or HYDRO_FP32 */
     int hse_subtract;
     int scheme;          /* HYDRO_SCHEME_HANCOCK (0) or HYDRO_SCHEME_SSPRK2 */
+    int recon;           /* HYDRO_RECON_PLM (0) or HYDRO_RECON_PPM */
 } hydro_problem;
 
 typedef struct hydro_sim hydro_sim;

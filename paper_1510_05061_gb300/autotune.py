@@ -117,6 +117,8 @@ def sim_signature(sim) -> str:
     p = sim.prob
     prec = "fp32" if p.precision == inputs.FP32 else "fp64"
     scheme = "rk2" if getattr(p, "scheme", 0) == inputs.SSPRK2 else "hancock"
+    if getattr(p, "recon", 0) == inputs.PPM:
+        scheme += "-ppm"
     return (f"{torch.cuda.get_device_name()}|single|{prec}|hse{p.hse_subtract}|{scheme}"
             f"|n={p.n[0]}x{p.n[1]}x{p.n[2]}")
 

@@ -72,6 +72,13 @@ int check_problem(const hydro_problem *p)
     if (p->precision != HYDRO_FP64 && p->precision != HYDRO_FP32) return HYDRO_ERR_INVALID_ARG;
     if (p->hse_subtract != 0 && p->hse_subtract != 1) return HYDRO_ERR_INVALID_ARG;
     if (p->scheme != HYDRO_SCHEME_HANCOCK && p->scheme != HYDRO_SCHEME_SSPRK2) return HYDRO_ERR_INVALID_ARG;
+    if (p->recon != HYDRO_RECON_PLM && p->recon != HYDRO_RECON_PPM) return HYDRO_ERR_INVALID_ARG;
+    if (p->recon == HYDRO_RECON_PPM) {
+        // three-cell halo: every active axis needs three cells to map into
+        if (p->scheme != HYDRO_SCHEME_SSPRK2 || p->hse_subtract) return HYDRO_ERR_INVALID_ARG;
+        for (int d = 0; d < p->ndim; ++d)
+            if (p->n[d] < 3) return HYDRO_ERR_INVALID_ARG;
+    }
     if (p->hse_subtract && (p->ndim != 3 || p->grav[0] != 0.0 || p->grav[1] != 0.0))
         return HYDRO_ERR_INVALID_ARG;
     // 32-bit plane and cell indexing inside a plane; 64-bit across planes
@@ -189,13 +196,15 @@ cudaError_t launch_kernel(hydro_sim *s, const StepArgs &a, int stage)
     const bool fp32 = s->prob.precision == HYDRO_FP32;
     const bool hse = s->prob.hse_subtract != 0;
     s->launches += 1;
-    if (s->prob.ndim == 2) return launch_step2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32, stage);
+    const int recon = s->prob.recon;
+    if (s->prob.ndim == 2)
+        return launch_step2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32, stage, recon);
     const dim3 grid(s->tiles_x * s->tiles_y, (s->prob.n[2] + s->zchunk - 1) / s->zchunk);
     if (stage == STAGE_HANCOCK)
         return fp32 ? launch_step3d_f32(s->variant, a, grid, s->stream, hse)
                     : launch_step3d_f64(s->variant, a, grid, s->stream, hse);
-    return fp32 ? launch_stage3d_f32(stage, s->variant, a, grid, s->stream, hse)
-                : launch_stage3d_f64(stage, s->variant, a, grid, s->stream, hse);
+    return fp32 ? launch_stage3d_f32(stage, s->variant, a, grid, s->stream, hse, recon)
+                : launch_stage3d_f64(stage, s->variant, a, grid, s->stream, hse, recon);
 }
 
 int launch_step(hydro_sim *s, double t_end)

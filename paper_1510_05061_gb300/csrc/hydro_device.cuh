@@ -239,6 +239,27 @@ __device__ __forceinline__ void mol_faces(const T (&w)[ND + 2], T (&dw)[ND][ND +
     }
 }
 
+// Piecewise parabolic face values (Colella and Woodward 1984, uniform grid)
+// of the cell with value a, face neighbours am and ap and MC-limited slopes
+// sm, s, sp (cells i-1, i, i+1): interface values (a + a')/2 - (s' - s)/6,
+// then the parabola limited to be monotone: flat at a local extremum, else
+// a face value moved so that the parabola has no interior extremum.
+template <typename T>
+__device__ __forceinline__ void ppm_faces(T am, T a, T ap, T sm, T s, T sp, T &lo, T &hi)
+{
+    const T sixth = T(1.0 / 6.0);
+    T aL = T(0.5) * (am + a) - (s - sm) * sixth;
+    T aR = T(0.5) * (a + ap) - (sp - s) * sixth;
+    const bool flat = (aR - a) * (a - aL) <= T(0);
+    const T da = aR - aL;
+    const T a6 = T(6) * (a - T(0.5) * (aL + aR));
+    const T dd = da * da, d6 = da * a6;
+    const bool fix_l = !flat && d6 > dd;
+    const bool fix_r = !flat && !fix_l && -dd > d6;
+    lo = flat ? a : (fix_l ? T(3) * a - T(2) * aR : aL);
+    hi = flat ? a : (fix_r ? T(3) * a - T(2) * aL : aR);
+}
+
 // HLLC flux along axis D (Toro, 3rd ed., sec. 10.4-10.6) with Davis wave
 // speeds S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R).
 // wl, wr hold (rho', u, p') and (rb, pb) the background at the face; in plain

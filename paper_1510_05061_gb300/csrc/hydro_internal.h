@@ -85,4 +85,8 @@ struct WorkLayout {
 // stage of the SSP-RK2 method of lines.
 enum { STAGE_HANCOCK = 0, STAGE_RK1 = 1, STAGE_RK2 = 2 };
 
+// Reconstruction of the face states: MC-limited linear, or the piecewise
+// parabolic method (method-of-lines stages, no background subtraction).
+enum { RECON_PLM = 0, RECON_PPM = 1 };
+
 }  // namespace hydro

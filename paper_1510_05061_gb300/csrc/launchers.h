@@ -47,11 +47,15 @@ int batch2d_max_grid(bool fp32);
 // single-solve 3D step with tile variant v (grid = tiles x z-chunks)
 cudaError_t launch_step3d_f64(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
 cudaError_t launch_step3d_f32(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
-// stage = STAGE_RK1 or STAGE_RK2 of the SSP-RK2 method of lines
-cudaError_t launch_stage3d_f64(int stage, int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
-cudaError_t launch_stage3d_f32(int stage, int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
-// stage: STAGE_HANCOCK, STAGE_RK1 or STAGE_RK2
-cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32, int stage = STAGE_HANCOCK);
+// stage = STAGE_RK1 or STAGE_RK2 of the SSP-RK2 method of lines; recon =
+// RECON_PLM or RECON_PPM (PPM without background subtraction)
+cudaError_t launch_stage3d_f64(int stage, int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse,
+                               int recon);
+cudaError_t launch_stage3d_f32(int stage, int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse,
+                               int recon);
+// stage: STAGE_HANCOCK, STAGE_RK1 or STAGE_RK2; recon as above (stages only)
+cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32, int stage = STAGE_HANCOCK,
+                          int recon = RECON_PLM);
 
 // Auxiliary kernels (aux.cu).  fp32 selects the stored precision.
 struct AuxArgs {

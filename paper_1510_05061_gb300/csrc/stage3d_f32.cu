@@ -1,5 +1,6 @@
 // stage3d_f32.cu -- FP32 instantiations of the two stages of the SSP-RK2
-// method of lines (3D, every tile shape).
+// method of lines (3D, every tile shape; PLM with and without background
+// subtraction, PPM without).
 #include "launchers.h"
 #include "step3d.cuh"
 
@@ -7,11 +8,11 @@ namespace hydro {
 
 namespace {
 
-template <int ST, bool HSE, int TX, int TY>
+template <int ST, int RC, bool HSE, int TX, int TY>
 cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
-    auto k = step3d_kernel<float, HSE, TX, TY, ST>;
-    constexpr size_t smem = Step3DSmem<float, HSE, TX, TY>::bytes;
+    auto k = step3d_kernel<float, HSE, TX, TY, ST, RC>;
+    constexpr size_t smem = Step3DSmem<float, HSE, TX, TY, RC>::bytes;
     static bool configured = false;   // the attribute is per function
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -22,30 +23,32 @@ cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int ST, bool HSE>
+template <int ST, int RC, bool HSE>
 cudaError_t launch_v(int v, const StepArgs &a, dim3 grid, cudaStream_t s)
 {
     switch (v) {
-    case 0: return launch3d<ST, HSE, 32, 8>(a, grid, s);
-    case 1: return launch3d<ST, HSE, 32, 4>(a, grid, s);
-    case 2: return launch3d<ST, HSE, 16, 16>(a, grid, s);
-    case 3: return launch3d<ST, HSE, 32, 16>(a, grid, s);
+    case 0: return launch3d<ST, RC, HSE, 32, 8>(a, grid, s);
+    case 1: return launch3d<ST, RC, HSE, 32, 4>(a, grid, s);
+    case 2: return launch3d<ST, RC, HSE, 16, 16>(a, grid, s);
+    case 3: return launch3d<ST, RC, HSE, 32, 16>(a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <int ST>
-cudaError_t launch_h(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse)
+cudaError_t launch_h(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse, int recon)
 {
-    return hse ? launch_v<ST, true>(v, a, grid, s) : launch_v<ST, false>(v, a, grid, s);
+    if (recon == RECON_PPM)
+        return hse ? cudaErrorInvalidValue : launch_v<ST, RECON_PPM, false>(v, a, grid, s);
+    return hse ? launch_v<ST, RECON_PLM, true>(v, a, grid, s) : launch_v<ST, RECON_PLM, false>(v, a, grid, s);
 }
 
 }  // namespace
 
-cudaError_t launch_stage3d_f32(int stage, int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse)
+cudaError_t launch_stage3d_f32(int stage, int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse, int recon)
 {
-    if (stage == STAGE_RK1) return launch_h<STAGE_RK1>(v, a, grid, s, hse);
-    if (stage == STAGE_RK2) return launch_h<STAGE_RK2>(v, a, grid, s, hse);
+    if (stage == STAGE_RK1) return launch_h<STAGE_RK1>(v, a, grid, s, hse, recon);
+    if (stage == STAGE_RK2) return launch_h<STAGE_RK2>(v, a, grid, s, hse, recon);
     return cudaErrorInvalidValue;
 }
 

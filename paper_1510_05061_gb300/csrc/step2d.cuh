@@ -15,10 +15,11 @@
 
 namespace hydro {
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int RC = RECON_PLM>
 struct Step2DSmem {
     static constexpr int NV = 4;
-    static constexpr int HX = TX + 4, HY = TY + 4;
+    static constexpr int H = RC == RECON_PPM ? 3 : 2;   // halo depth
+    static constexpr int HX = TX + 2 * H, HY = TY + 2 * H;
     static constexpr size_t prim = (size_t)NV * HY * HX;
     static constexpr size_t wx = (size_t)NV * TY * (TX + 2);
     static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;
@@ -43,14 +44,16 @@ __device__ __forceinline__ void step2d_copy(const StepArgs &a, int tile, const v
 }
 
 // One CTA's share of a 2D step: tile `tile` (row-major over tiles_x).  ST
-// selects the MUSCL-Hancock step or a Runge-Kutta stage as in step3d_body.
-template <typename T, int TX, int TY, int ST = STAGE_HANCOCK>
+// selects the MUSCL-Hancock step or a Runge-Kutta stage and RC the face
+// states (MC-limited linear or PPM) as in step3d_body.
+template <typename T, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
 __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 2, NV = 4, NT = TX * TY;
-    using S = Step2DSmem<T, TX, TY>;
-    constexpr int HX = S::HX, HY = S::HY;
+    static_assert(RC == RECON_PLM || ST != STAGE_HANCOCK, "PPM: method-of-lines stages");
+    using S = Step2DSmem<T, TX, TY, RC>;
+    constexpr int HX = S::HX, HY = S::HY, H = S::H;
     T *prim = reinterpret_cast<T *>(smem_raw);
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
@@ -86,8 +89,8 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     for (int i = tid; i < HX * HY; i += NT) {
         const int hx = i % HX, hy = i / HX;
         bool fx, fy;
-        const int sx = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
-        const int sy = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
+        const int sx = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
+        const int sy = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
         const size_t c = (size_t)sy * nx + sx;
         const T r = U[c];
         T m0 = U[c + vs], m1 = U[c + 2 * vs];
@@ -104,7 +107,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
 
     const CellBG<T> nobg = cell_bg<T, false>(static_cast<const PlaneBGT<T> *>(nullptr), 0);
     auto predict = [&](int cx, int cy, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
-        const int hx = cx + 2, hy = cy + 2;
+        const int hx = cx + H, hy = cy + H;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             const T c = P(q, hy, hx);
@@ -121,8 +124,31 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
         }
     };
 
+    // PPM face states along axis d of variable q (see step3d_body)
+    auto ppm_dir = [&](int cx, int cy, int d, int q, T &lo, T &hi) {
+        const int hx = cx + H, hy = cy + H;
+        T v[5];
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) v[k + 2] = d == 0 ? P(q, hy, hx + k) : P(q, hy + k, hx);
+        const T sm = mc_slope(v[1] - v[0], v[2] - v[1]);
+        const T s0 = mc_slope(v[2] - v[1], v[3] - v[2]);
+        const T sp = mc_slope(v[3] - v[2], v[4] - v[3]);
+        ppm_faces(v[1], v[2], v[3], sm, s0, sp, lo, hi);
+    };
+
     // ---- half step: tile cells, then the cross-shaped ring
-    {
+    if constexpr (RC == RECON_PPM) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            T lo, hi;
+            ppm_dir(tx, ty, 0, q, lo, hi);
+            WX(wxl, q, ty, tx) = lo;
+            WX(wxh, q, ty, tx) = hi;
+            ppm_dir(tx, ty, 1, q, lo, hi);
+            WY(wyl, q, ty, tx) = lo;
+            WY(wyh, q, ty, tx) = hi;
+        }
+    } else {
         T w[NV], dw[ND][NV], wh[NV];
         predict(tx, ty, w, dw, wh);
 #pragma unroll
@@ -139,6 +165,21 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
         bool xside;
         if (i < 2 * TY) { xside = true; cy = i >> 1; cx = (i & 1) ? TX : -1; }
         else { xside = false; const int j = i - 2 * TY; cx = j >> 1; cy = (j & 1) ? TY : -1; }
+        if constexpr (RC == RECON_PPM) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                T lo, hi;
+                ppm_dir(cx, cy, xside ? 0 : 1, q, lo, hi);
+                if (xside) {
+                    if (cx < 0) WX(wxh, q, cy, cx) = hi;
+                    else WX(wxl, q, cy, cx) = lo;
+                } else {
+                    if (cy < 0) WY(wyh, q, cy, cx) = hi;
+                    else WY(wyl, q, cy, cx) = lo;
+                }
+            }
+            continue;
+        }
         T w[NV], dw[ND][NV], wh[NV];
         predict(cx, cy, w, dw, wh);
         if (xside) {
@@ -255,7 +296,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     }
 }
 
-template <typename T, int TX, int TY, int ST = STAGE_HANCOCK>
+template <typename T, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
 __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
@@ -272,7 +313,7 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    step2d_body<T, TX, TY, ST>(a, blockIdx.x, dtd, smem_raw, smax, bad);
+    step2d_body<T, TX, TY, ST, RC>(a, blockIdx.x, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
         if (bad_cta && threadIdx.x == 0) atomicOr(&a.ctrl->err_new, 1);

@@ -32,23 +32,30 @@
 #define HYDRO_ASYNC_STAGING 1
 #endif
 
-// Build option: minimum resident CTAs per SM asked of the FP64 kernels
-// (trades registers for occupancy).
+// Build options: minimum resident CTAs per SM asked of the FP64 kernels and
+// of the FP32 kernels of up to 256 threads (trade registers for occupancy).
 #ifndef HYDRO_FP64_MIN_CTAS
 #define HYDRO_FP64_MIN_CTAS 1
+#endif
+#ifndef HYDRO_FP32_MIN_CTAS
+#define HYDRO_FP32_MIN_CTAS 2
 #endif
 
 namespace hydro {
 
-template <typename T, bool HSE, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY, int RC = RECON_PLM>
 struct Step3DSmem {
     static constexpr int NV = 5;
-    static constexpr int HX = TX + 4, HY = TY + 4;
+    // halo depth and primitive ring: PLM needs cells i-2..i+2 for the faces
+    // of a face neighbour (ring of planes p-1..p+1), PPM i-3..i+3 (p-2..p+2)
+    static constexpr int H = RC == RECON_PPM ? 3 : 2;
+    static constexpr int NR = RC == RECON_PPM ? 5 : 3;
+    static constexpr int HX = TX + 2 * H, HY = TY + 2 * H;
     // Row stride of the staged planes.  A warp of a 16-wide tile spans two
     // rows; for 4-byte values a stride = 16 (mod 32) puts them on disjoint
     // shared-memory banks.  (8-byte values take one wavefront per row.)
     static constexpr int HXS = (TX == 16 && sizeof(T) == 4) ? 48 : HX;
-    static constexpr size_t prim = 3ull * NV * HY * HXS;       // [3][NV][HY][HXS]
+    static constexpr size_t prim = (size_t)NR * NV * HY * HXS; // [NR][NV][HY][HXS]
     static constexpr size_t wx = (size_t)NV * TY * (TX + 2);   // [NV][TY][TX+2]
     static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;   // [NV][TY+2][TX]
     static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
@@ -58,6 +65,7 @@ struct Step3DSmem {
     static constexpr size_t raw = async ? 2ull * NV * HX * HY : 0;   // [2][NV][HY*HX]
     static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy + raw;
     static constexpr size_t bytes = elems * sizeof(T);
+    static_assert(bytes <= 226 * 1024, "shared memory of one CTA");
 };
 
 // Asynchronous 4- or 8-byte global->shared copy (cp.async, cached in L1 and
@@ -101,14 +109,19 @@ __device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chu
 // Runge-Kutta stage U1 = U + dt L(U); or the second, (U0 + U + dt L(U)) / 2
 // with U = U1 and U0 = U^n.  The stages have no half-step predictor and
 // take the gravity source on the momentum from the stage's own density.
-template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK>
+// RC selects the face states: MC-limited linear (RECON_PLM), or piecewise
+// parabolic (RECON_PPM, Runge-Kutta stages without background only).
+template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
 __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chunk, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
-    using S = Step3DSmem<T, HSE, TX, TY>;
+    static_assert(RC == RECON_PLM || (ST != STAGE_HANCOCK && !HSE), "PPM: method-of-lines stages, no background");
+    using S = Step3DSmem<T, HSE, TX, TY, RC>;
     constexpr bool ASYNC = S::async;
-    constexpr int HX = S::HX, HY = S::HY;
+    constexpr int HX = S::HX, HY = S::HY, H = S::H, NR = S::NR;
+    // planes staged ahead of the plane whose face states are computed
+    constexpr int LEAD = H - 1;
     T *prim = reinterpret_cast<T *>(smem_raw);
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
@@ -154,8 +167,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         const int i = tid + j * NT;
         const int hx = i % HX, hy = i / HX;
         bool fx, fy;
-        const int gxm = map_index(x0 + hx - 2, nx, a.bc_lo[0], a.bc_hi[0], fx);
-        const int gym = map_index(y0 + hy - 2, ny, a.bc_lo[1], a.bc_hi[1], fy);
+        const int gxm = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
+        const int gym = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
         xyoff[j] = gym * nx + gxm;
         flips |= (fx ? 1u : 0u) << (2 * j);
         flips |= (fy ? 1u : 0u) << (2 * j + 1);
@@ -184,7 +197,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         if constexpr (ASYNC) cp_async_commit();
     };
     auto store = [&](int pz) {
-        const int slot = (pz + 3) % 3;
+        const int slot = (pz + 2 * NR) % NR;
         const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
         bool fz;
         map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
@@ -215,8 +228,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
     // ---- slopes + half step of the cell at local (cx, cy) of plane p
     auto predict = [&](int cx, int cy, int p, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
-        const int s0 = (p + 3) % 3, sm = (p + 2) % 3, sp = (p + 4) % 3;
-        const int hx = cx + 2, hy = cy + 2;
+        const int s0 = (p + 2 * NR) % NR, sm = (p - 1 + 2 * NR) % NR, sp = (p + 1 + 2 * NR) % NR;
+        const int hx = cx + H, hy = cy + H;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             const T c = P(s0, q, hy, hx);
@@ -233,6 +246,25 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 #pragma unroll
             for (int q = 0; q < NV; ++q) wh[q] = w[q];
         }
+    };
+
+    // ---- PPM face states of the cell at local (cx, cy) of plane p along
+    // axis d for variable q.  The limited faces lie between the cell and its
+    // neighbours, so positive densities and pressures stay positive and the
+    // positivity fallback of the linear states is never needed.
+    auto ppm_dir = [&](int cx, int cy, int p, int d, int q, T &lo, T &hi) {
+        const int hx = cx + H, hy = cy + H;
+        T v[5];
+#pragma unroll
+        for (int k = -2; k <= 2; ++k) {
+            if (d == 0) v[k + 2] = P((p + 2 * NR) % NR, q, hy, hx + k);
+            else if (d == 1) v[k + 2] = P((p + 2 * NR) % NR, q, hy + k, hx);
+            else v[k + 2] = P((p + k + 2 * NR) % NR, q, hy, hx);
+        }
+        const T sm = mc_slope(v[1] - v[0], v[2] - v[1]);
+        const T s0 = mc_slope(v[2] - v[1], v[3] - v[2]);
+        const T sp = mc_slope(v[3] - v[2], v[4] - v[3]);
+        ppm_faces(v[1], v[2], v[3], sm, s0, sp, lo, hi);
     };
 
     auto WX = [&](T *base, int q, int cy, int cx) -> T & {   // cx in [-1, TX]
@@ -254,23 +286,25 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
 
-    fetch(z0 - 2);
-    store(z0 - 2);
-    fetch(z0 - 1);
-    store(z0 - 1);
+    // planes z0-H .. z0+LEAD-2 before the march; iteration p stages p+LEAD
+    for (int pz = z0 - H; pz <= z0 + LEAD - 2; ++pz) {
+        fetch(pz);
+        store(pz);
+    }
     if constexpr (ASYNC) {
         __syncthreads();
-        fetch(z0);
+        fetch(z0 + LEAD - 1);
     }
     for (int p = z0 - 1; p <= z1; ++p) {
         if constexpr (ASYNC) {
-            // plane p+1 was requested one iteration ago; request p+2 into the
-            // buffer plane p used (converted before the last barrier)
-            store(p + 1);
-            if (p + 2 <= z1 + 1) fetch(p + 2);
+            // plane p+LEAD was requested one iteration ago; request the next
+            // one into the buffer the previous plane used (converted before
+            // the last barrier)
+            store(p + LEAD);
+            if (p + LEAD + 1 <= z1 + LEAD) fetch(p + LEAD + 1);
         } else {
-            fetch(p + 1);
-            store(p + 1);
+            fetch(p + LEAD);
+            store(p + LEAD);
         }
         __syncthreads();
         const bool xy = (p >= z0 && p < z1);
@@ -296,7 +330,22 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
         // ---- step 2: half step; own cell first (z faces kept in registers)
         T zlo[NV], ztop[NV];
-        {
+        if constexpr (RC == RECON_PPM) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) ppm_dir(tx, ty, p, 2, q, zlo[q], ztop[q]);
+            if (xy) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    T lo, hi;
+                    ppm_dir(tx, ty, p, 0, q, lo, hi);
+                    WX(wxl, q, ty, tx) = lo;
+                    WX(wxh, q, ty, tx) = hi;
+                    ppm_dir(tx, ty, p, 1, q, lo, hi);
+                    WY(wyl, q, ty, tx) = lo;
+                    WY(wyh, q, ty, tx) = hi;
+                }
+            }
+        } else {
             T w[NV], dw[ND][NV], wh[NV];
             predict(tx, ty, p, w, dw, wh);
 #pragma unroll
@@ -323,6 +372,21 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                 bool xside;
                 if (i < 2 * TY) { xside = true; cy = i >> 1; cx = (i & 1) ? TX : -1; }
                 else { xside = false; const int j = i - 2 * TY; cx = j >> 1; cy = (j & 1) ? TY : -1; }
+                if constexpr (RC == RECON_PPM) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        T lo, hi;
+                        ppm_dir(cx, cy, p, xside ? 0 : 1, q, lo, hi);
+                        if (xside) {
+                            if (cx < 0) WX(wxh, q, cy, cx) = hi;
+                            else WX(wxl, q, cy, cx) = lo;
+                        } else {
+                            if (cy < 0) WY(wyh, q, cy, cx) = hi;
+                            else WY(wyl, q, cy, cx) = lo;
+                        }
+                    }
+                    continue;
+                }
                 T w[NV], dw[ND][NV], wh[NV];
                 predict(cx, cy, p, w, dw, wh);
                 if (xside) {
@@ -535,8 +599,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
 }
 
-template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 : 1) : HYDRO_FP64_MIN_CTAS) step3d_kernel(const StepArgs a)
+template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? HYDRO_FP32_MIN_CTAS : 1) : HYDRO_FP64_MIN_CTAS) step3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -557,7 +621,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    step3d_body<T, HSE, TX, TY, ST>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    step3d_body<T, HSE, TX, TY, ST, RC>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
         // the intermediate state only raises error bits; dt and time move
@@ -575,7 +639,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 
 // own time-control block; the CTA that completes the instance's last item
 // sets that instance's next dt (per-instance CFL).
 template <typename T, bool HSE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? 2 : 1) : HYDRO_FP64_MIN_CTAS)
+__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? HYDRO_FP32_MIN_CTAS : 1) : HYDRO_FP64_MIN_CTAS)
 step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
                     int nitems, int parity)
 {

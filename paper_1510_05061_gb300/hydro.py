@@ -62,7 +62,7 @@ class hydro_problem(C.Structure):
         ("lo", C.c_double * 3), ("hi", C.c_double * 3),
         ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3),
         ("gamma", C.c_double), ("cfl", C.c_double), ("grav", C.c_double * 3),
-        ("precision", C.c_int), ("hse_subtract", C.c_int), ("scheme", C.c_int),
+        ("precision", C.c_int), ("hse_subtract", C.c_int), ("scheme", C.c_int), ("recon", C.c_int),
     ]
 
 
@@ -217,6 +217,7 @@ def make_problem(p: "inputs.Problem") -> hydro_problem:
     s.precision = int(p.precision)
     s.hse_subtract = int(p.hse_subtract)
     s.scheme = int(getattr(p, "scheme", 0))
+    s.recon = int(getattr(p, "recon", 0))
     return s
 
 
