@@ -75,15 +75,15 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(0)};
     const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(0)};
 
-    auto P = [&](int q, int hy, int hx) -> T & { return prim[((size_t)q * HY + hy) * HX + hx]; };
+    auto P = [&](int q, int hy, int hx) -> T & { return prim[(q * HY + hy) * HX + hx]; };
     auto WX = [&](T *base, int q, int cy, int cx) -> T & {
-        return base[((size_t)q * TY + cy) * (TX + 2) + cx + 1];
+        return base[(q * TY + cy) * (TX + 2) + cx + 1];
     };
     auto WY = [&](T *base, int q, int cy, int cx) -> T & {
-        return base[((size_t)q * (TY + 2) + cy + 1) * TX + cx];
+        return base[(q * (TY + 2) + cy + 1) * TX + cx];
     };
-    auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[((size_t)q * TY + cy) * (TX + 1) + fxi]; };
-    auto FY = [&](int q, int fyi, int cx) -> T & { return fys[((size_t)q * (TY + 1) + fyi) * TX + cx]; };
+    auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[(q * TY + cy) * (TX + 1) + fxi]; };
+    auto FY = [&](int q, int fyi, int cx) -> T & { return fys[(q * (TY + 1) + fyi) * TX + cx]; };
 
     // ---- stage the haloed tile as primitives
     for (int i = tid; i < HX * HY; i += NT) {
@@ -91,7 +91,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
         bool fx, fy;
         const int sx = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
         const int sy = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
-        const size_t c = (size_t)sy * nx + sx;
+        const int c = sy * nx + sx;   // a plane holds fewer than 2^31 cells
         const T r = U[c];
         T m0 = U[c + vs], m1 = U[c + 2 * vs];
         const T e = U[c + 3 * vs];
@@ -262,7 +262,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     smax = T(0);
     bad = false;
     if (own) {
-        const size_t c = (size_t)gy * nx + gx;
+        const int c = gy * nx + gx;
         T u[NV], du[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {

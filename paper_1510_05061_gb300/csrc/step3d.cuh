@@ -34,12 +34,21 @@
 
 // Build options: minimum resident CTAs per SM asked of the FP64 kernels and
 // of the FP32 kernels of up to 256 threads (trade registers for occupancy).
+// The FP32 32 x 8 tile asks for three (80 registers, measured +5 % on
+// GB300 at 512^3 over two); the other FP32 tiles lose with three.
 #ifndef HYDRO_FP64_MIN_CTAS
 #define HYDRO_FP64_MIN_CTAS 1
 #endif
 #ifndef HYDRO_FP32_MIN_CTAS
 #define HYDRO_FP32_MIN_CTAS 2
 #endif
+#ifndef HYDRO_FP32_32X8_MIN_CTAS
+#define HYDRO_FP32_32X8_MIN_CTAS 3
+#endif
+#define HYDRO_STEP3D_MIN_CTAS(T, TX, TY)                                                                 \
+    (sizeof(T) == 4 ? ((TX) * (TY) > 256 ? 1 : ((TX) == 32 && (TY) == 8 ? HYDRO_FP32_32X8_MIN_CTAS      \
+                                                                          : HYDRO_FP32_MIN_CTAS))      \
+                    : HYDRO_FP64_MIN_CTAS)
 
 namespace hydro {
 
@@ -138,6 +147,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     const T *__restrict__ U0 = static_cast<const T *>(a.U0);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
     const long long vs = a.vstride;
+    // plane offsets as 32 x 32 -> 64-bit products (a plane holds fewer than
+    // 2^31 cells); 64 x 64-bit multiplies would occupy the FP64 pipe
+    const int plane = static_cast<int>(a.plane);
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
     const T gam = T(a.gamma);
     const T igm1 = T(1.0 / (a.gamma - 1.0));
@@ -147,7 +159,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
     constexpr int HXS = S::HXS;
     auto P = [&](int slot, int q, int hy, int hx) -> T & {
-        return prim[((size_t)(slot * NV + q) * HY + hy) * HXS + hx];
+        return prim[((slot * NV + q) * HY + hy) * HXS + hx];   // 32-bit shared-memory indices
     };
 
     // ---- stage plane pz (may be a ghost plane) into its ring slot, in two
@@ -178,8 +190,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         bool fz;
         const int gz = map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
         // gz is -2 or -1 below a halo side: signed plane offset
-        const T *Up = U + (long long)gz * a.plane;
-        T *rb = rawbuf + (size_t)((pz + 4) & 1) * (NV * HXY);
+        const T *Up = U + (long long)gz * plane;
+        T *rb = rawbuf + ((pz + 4) & 1) * (NV * HXY);
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
             const int i = tid + j * NT;
@@ -201,7 +213,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
         bool fz;
         map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
-        const T *rb = rawbuf + (size_t)((pz + 4) & 1) * (NV * HXY);
+        const T *rb = rawbuf + ((pz + 4) & 1) * (NV * HXY);
         if constexpr (ASYNC) cp_async_wait_all();
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
@@ -268,13 +280,13 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     };
 
     auto WX = [&](T *base, int q, int cy, int cx) -> T & {   // cx in [-1, TX]
-        return base[((size_t)q * TY + cy) * (TX + 2) + cx + 1];
+        return base[(q * TY + cy) * (TX + 2) + cx + 1];
     };
     auto WY = [&](T *base, int q, int cy, int cx) -> T & {   // cy in [-1, TY]
-        return base[((size_t)q * (TY + 2) + cy + 1) * TX + cx];
+        return base[(q * (TY + 2) + cy + 1) * TX + cx];
     };
-    auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[((size_t)q * TY + cy) * (TX + 1) + fxi]; };
-    auto FY = [&](int q, int fyi, int cx) -> T & { return fys[((size_t)q * (TY + 1) + fyi) * TX + cx]; };
+    auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[(q * TY + cy) * (TX + 1) + fxi]; };
+    auto FY = [&](int q, int fyi, int cx) -> T & { return fys[(q * (TY + 1) + fyi) * TX + cx]; };
 
     // register pipeline of the thread's own column
     T ztop_prev[NV], fz_prev[NV], div_prev[NV];
@@ -285,6 +297,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     bad = false;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
+    const int own_off = gy * nx + gx;   // the thread's cell within a plane
 
     // planes z0-H .. z0+LEAD-2 before the march; iteration p stages p+LEAD
     for (int pz = z0 - H; pz <= z0 + LEAD - 2; ++pz) {
@@ -314,7 +327,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         T ufin[NV], u0fin[NV];
         T bgB = T(0), bgR = T(0), bgP = T(0);
         if (fin) {
-            const size_t c = (size_t)(p - 1) * a.plane + (size_t)gy * nx + gx;
+            const long long c = (long long)(p - 1) * plane + own_off;
 #pragma unroll
             for (int q = 0; q < NV; ++q) ufin[q] = U[c + q * vs];
             if constexpr (ST == STAGE_RK2) {
@@ -543,7 +556,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         // ---- step 4: complete plane p-1 (an output plane when p > z0)
         if (fin) {
             const int k = p - 1;
-            const size_t c = (size_t)k * a.plane + (size_t)gy * nx + gx;
+            const long long c = (long long)k * plane + own_off;
             T u[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) u[q] = ufin[q];
@@ -600,7 +613,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 }
 
 template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? HYDRO_FP32_MIN_CTAS : 1) : HYDRO_FP64_MIN_CTAS) step3d_kernel(const StepArgs a)
+__global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) step3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -639,7 +652,7 @@ __global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? HY
 // own time-control block; the CTA that completes the instance's last item
 // sets that instance's next dt (per-instance CFL).
 template <typename T, bool HSE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, sizeof(T) == 4 ? (TX * TY <= 256 ? HYDRO_FP32_MIN_CTAS : 1) : HYDRO_FP64_MIN_CTAS)
+__global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY))
 step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
                     int nitems, int parity)
 {
