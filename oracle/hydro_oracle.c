@@ -35,6 +35,17 @@
  * flux divergence, momentum source g rho of the stage state and the same
  * mass-flux energy source.  dt is taken from U^n.
  *
+ * Third integrator (scheme = 2, PLM and hse = 0 only): the unsplit corner
+ * transport upwind method of Colella (1990): per axis d a one-dimensional
+ * MUSCL-Hancock predictor (only the axis's own A_d term, half a step of
+ * gravity) gives face states; HLLC fluxes from those states at every face
+ * (first pass); each face state is corrected in conserved variables by the
+ * transverse flux differences of its own cell, -dt/(2 dx_e) (F_e(+) -
+ * F_e(-)) for every other axis e (kept uncorrected for a cell whose
+ * corrected pair along d would have a non-positive density or pressure);
+ * HLLC again on the corrected states; the update and sources of the
+ * MUSCL-Hancock step.
+ *
  * Second reconstruction (recon = 1, with scheme = 1 and hse = 0 only): the
  * piecewise parabolic method of Colella and Woodward (1984) in primitive
  * variables, used as the method of lines' face states: the interface value
@@ -72,7 +83,9 @@
 #define MAXV 5
 
 enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2 };
-enum { SCHEME_HANCOCK = 0, SCHEME_SSPRK2 = 1 };
+enum { SCHEME_HANCOCK = 0, SCHEME_SSPRK2 = 1, SCHEME_CTU = 2 };
+/* what one call of step_with does */
+enum { MODE_STAGE = 0, MODE_HANCOCK = 1, MODE_CTU = 2 };
 enum { RECON_PLM = 0, RECON_PPM = 1 };
 enum { OK = 0, ERR_ARG = -1, ERR_OOM = -2, ERR_NONPHYSICAL = -4 };
 
@@ -132,7 +145,8 @@ static int check_params(const orc_params *p)
         if (!(p->hi[d] > p->lo[d])) return ERR_ARG;
     }
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return ERR_ARG;
-    if (p->scheme != SCHEME_HANCOCK && p->scheme != SCHEME_SSPRK2) return ERR_ARG;
+    if (p->scheme != SCHEME_HANCOCK && p->scheme != SCHEME_SSPRK2 && p->scheme != SCHEME_CTU) return ERR_ARG;
+    if (p->scheme == SCHEME_CTU && (p->hse || p->recon != RECON_PLM)) return ERR_ARG;
     if (p->recon != RECON_PLM && p->recon != RECON_PPM) return ERR_ARG;
     if (p->recon == RECON_PPM) {
         if (p->scheme != SCHEME_SSPRK2 || p->hse) return ERR_ARG;
@@ -385,11 +399,12 @@ typedef struct {
     double *dW;     /* MC slopes, [d][q]                             ndim*nvar */
     double *Wf;     /* face states, [d][side][q]; side 0 = low face  2*ndim*nvar */
     double *F;      /* fluxes through the high face of each cell, [d][q] */
+    double *F1;     /* corner transport upwind: first-pass fluxes, [d][q] */
 } work_t;
 
 static void work_free(work_t *w)
 {
-    free(w->G); free(w->W); free(w->dW); free(w->Wf); free(w->F);
+    free(w->G); free(w->W); free(w->dW); free(w->Wf); free(w->F); free(w->F1);
     memset(w, 0, sizeof(*w));
 }
 
@@ -404,6 +419,10 @@ static int work_alloc(const orc_params *p, work_t *w)
     w->dW = (double *)calloc((size_t)nd * nv, a);
     w->Wf = (double *)calloc((size_t)2 * nd * nv, a);
     w->F = (double *)calloc((size_t)nd * nv, a);
+    if (p->scheme == SCHEME_CTU) {
+        w->F1 = (double *)calloc((size_t)nd * nv, a);
+        if (!w->F1) { work_free(w); return ERR_OOM; }
+    }
     if (!w->G || !w->W || !w->dW || !w->Wf || !w->F) { work_free(w); return ERR_OOM; }
     return OK;
 }
@@ -411,12 +430,119 @@ static int work_alloc(const orc_params *p, work_t *w)
 /* padded z-plane kk -> interior plane index k (may be outside [0, nz)) */
 static inline int zplane(const grid_t *g, int kk) { return kk - g->ng[2]; }
 
-/* One update U <- U + dt * (flux divergence + sources).  With predictor = 1
-   it is the MUSCL-Hancock step; with predictor = 0 it is one forward-Euler
-   stage U + dt L(U) of the method of lines (face states W -/+ dW/2, gravity
-   on the momentum from the stage density). */
-static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int predictor)
+/* HLLC flux through the high face of each cell along every axis d, from
+   the face states Wf, into F.  ext = 0: the faces of the interior (cells
+   ng-1 .. ng+n-1 along d, interior across); ext = 1: also one ring of cells
+   beyond the interior across d (the first pass of the corner transport
+   upwind method). */
+static void flux_pass(const orc_params *p, work_t *wk, const double *Wf, double *F, int ext)
 {
+    const grid_t *g = &wk->g;
+    const int nd = g->ndim, nv = g->nvar;
+    const long np = g->npad;
+    const double gam = p->gamma;
+    const int st[3] = {1, g->P[0], g->P[0] * g->P[1]};
+    for (int d = 0; d < nd; ++d) {
+        int flo[3], fhi[3];
+        for (int e = 0; e < 3; ++e) {
+            int x = (ext && e != d && g->ng[e] > 0) ? 1 : 0;
+            flo[e] = g->ng[e] - x;
+            fhi[e] = g->ng[e] + g->n[e] + x;
+        }
+        flo[d] -= 1;
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int kk = flo[2]; kk < fhi[2]; ++kk)
+            for (int j = flo[1]; j < fhi[1]; ++j) {
+                int k = zplane(g, kk);
+                for (int i = flo[0]; i < fhi[0]; ++i) {
+                    long c = pidx(g, i, j, kk);
+                    long cn = c + st[d];
+                    double wl[MAXV], wr[MAXV], f[MAXV];
+                    /* background at this face: the z face k+1/2, or the
+                       plane's centre value for x and y faces */
+                    double rb, pb;
+                    if (d == 2) { rb = bg_rho_face(p, k + 1); pb = bg_p_face(p, k + 1); }
+                    else        { rb = bg_rho_centre(p, k);   pb = bg_p_centre(p, k); }
+                    for (int q = 0; q < nv; ++q) {
+                        wl[q] = Wf[((d * 2 + 1) * nv + q) * np + c];
+                        wr[q] = Wf[((d * 2 + 0) * nv + q) * np + cn];
+                    }
+                    /* reflecting wall: the far side of the wall face is the
+                       mirror image of the interior cell's predicted face
+                       state (normal velocity negated), so no mass crosses it */
+                    int cd = d == 0 ? i : (d == 1 ? j : kk);
+                    if (cd == g->ng[d] - 1 && p->bc_lo[d] == BC_REFLECT) {
+                        for (int q = 0; q < nv; ++q) wl[q] = wr[q];
+                        wl[1 + d] = -wr[1 + d];
+                    }
+                    if (cd == g->ng[d] + g->n[d] - 1 && p->bc_hi[d] == BC_REFLECT) {
+                        for (int q = 0; q < nv; ++q) wr[q] = wl[q];
+                        wr[1 + d] = -wl[1 + d];
+                    }
+                    wl[0] += rb; wr[0] += rb;
+                    wl[nd + 1] += pb; wr[nd + 1] += pb;
+                    orc_hllc(nd, gam, d, wl, wr, f);
+                    f[1 + d] -= pb;   /* momentum flux carries p' */
+                    for (int q = 0; q < nv; ++q) F[(d * nv + q) * np + c] = f[q];
+                }
+            }
+    }
+}
+
+/* Corner transport upwind: correct the face states of every cell that
+   borders an interior face along d (cells ng-1 .. ng+n along d, interior
+   across) by the transverse differences of the first-pass fluxes of that
+   cell, in conserved variables; a cell whose corrected pair along d has a
+   non-positive density or pressure keeps its uncorrected pair. */
+static void ctu_correct(const orc_params *p, work_t *wk, double dt)
+{
+    const grid_t *g = &wk->g;
+    const int nd = g->ndim, nv = g->nvar;
+    const long np = g->npad;
+    const int st[3] = {1, g->P[0], g->P[0] * g->P[1]};
+    for (int d = 0; d < nd; ++d) {
+        int clo[3], chi[3];
+        for (int e = 0; e < 3; ++e) {
+            clo[e] = g->ng[e];
+            chi[e] = g->ng[e] + g->n[e];
+        }
+        clo[d] -= 1;
+        chi[d] += 1;
+        #pragma omp parallel for collapse(2) schedule(static)
+        for (int kk = clo[2]; kk < chi[2]; ++kk)
+            for (int j = clo[1]; j < chi[1]; ++j)
+                for (int i = clo[0]; i < chi[0]; ++i) {
+                    long c = pidx(g, i, j, kk);
+                    double wc[2][MAXV];
+                    int bad = 0;
+                    for (int s = 0; s < 2; ++s) {
+                        double w[MAXV], u[MAXV];
+                        for (int q = 0; q < nv; ++q) w[q] = wk->Wf[((d * 2 + s) * nv + q) * np + c];
+                        prim_to_cons(nd, p->gamma, w, u);
+                        for (int e = 0; e < nd; ++e) {
+                            if (e == d) continue;
+                            for (int q = 0; q < nv; ++q) {
+                                const double *Fq = wk->F1 + (e * nv + q) * np;
+                                u[q] -= dt / (2.0 * g->dx[e]) * (Fq[c] - Fq[c - st[e]]);
+                            }
+                        }
+                        cons_to_prim(nd, p->gamma, 0.0, u, wc[s]);
+                        if (!(wc[s][0] > 0.0) || !(wc[s][nd + 1] > 0.0)) bad = 1;
+                    }
+                    if (bad) continue;
+                    for (int s = 0; s < 2; ++s)
+                        for (int q = 0; q < nv; ++q) wk->Wf[((d * 2 + s) * nv + q) * np + c] = wc[s][q];
+                }
+    }
+}
+
+/* One update U <- U + dt * (flux divergence + sources).  mode MODE_HANCOCK:
+   the MUSCL-Hancock step; MODE_STAGE: one forward-Euler stage U + dt L(U)
+   of the method of lines (face states W -/+ dW/2, gravity on the momentum
+   from the stage density); MODE_CTU: the corner transport upwind step. */
+static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int mode)
+{
+    const int predictor = mode != MODE_STAGE;
     const grid_t *g = &wk->g;
     const int nd = g->ndim, nv = g->nvar;
     const long np = g->npad;
@@ -509,6 +635,20 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
                     for (int q = 0; q < nv; ++q) wh[q] = w[q] + hdt * dwdt[q];
                 else
                     for (int q = 0; q < nv; ++q) wh[q] = w[q];
+                /* corner transport upwind: per axis the one-dimensional
+                   predictor, only that axis's A_d term plus gravity */
+                double wd[3][MAXV];
+                if (mode == MODE_CTU)
+                    for (int d = 0; d < nd; ++d) {
+                        double r[MAXV] = {0};
+                        double un = w[1 + d];
+                        r[0] = -(un * dw[d][0] + rho * dw[d][1 + d]) / g->dx[d];
+                        for (int e = 0; e < nd; ++e) r[1 + e] = -un * dw[d][1 + e] / g->dx[d];
+                        r[1 + d] -= dw[d][nd + 1] / rho / g->dx[d];
+                        r[nd + 1] = -(un * dw[d][nd + 1] + gam * pr * dw[d][1 + d]) / g->dx[d];
+                        for (int e = 0; e < nd; ++e) r[1 + e] += p->grav[e] * (w[0] / rho);
+                        for (int q = 0; q < nv; ++q) wd[d][q] = w[q] + hdt * r[q];
+                    }
 
                 double wf[3][2][MAXV];
                 int bad = 0;
@@ -524,7 +664,9 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
                 for (int d = 0; d < nd; ++d)
                     for (int s = 0; s < 2; ++s) {
                         double sgn = s == 0 ? -0.5 : 0.5;
-                        if (p->recon == RECON_PLM)
+                        if (mode == MODE_CTU)
+                            for (int q = 0; q < nv; ++q) wf[d][s][q] = wd[d][q] + sgn * dw[d][q];
+                        else if (p->recon == RECON_PLM)
                             for (int q = 0; q < nv; ++q) wf[d][s][q] = wh[q] + sgn * dw[d][q];
                         /* totals at this face for the positivity test */
                         double rb = rho_bg, pb = p_bg;
@@ -553,52 +695,15 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
             }
         }
 
-    /* 5. HLLC flux through the high face of each cell along d,
-       for every face of the interior (cells ng-1 .. ng+n-1 along d) */
-    for (int d = 0; d < nd; ++d) {
-        int flo[3], fhi[3];
-        for (int e = 0; e < 3; ++e) {
-            flo[e] = g->ng[e];
-            fhi[e] = g->ng[e] + g->n[e];
-        }
-        flo[d] -= 1;
-        #pragma omp parallel for collapse(2) schedule(static)
-        for (int kk = flo[2]; kk < fhi[2]; ++kk)
-            for (int j = flo[1]; j < fhi[1]; ++j) {
-                int k = zplane(g, kk);
-                for (int i = flo[0]; i < fhi[0]; ++i) {
-                    long c = pidx(g, i, j, kk);
-                    long cn = c + st[d];
-                    double wl[MAXV], wr[MAXV], f[MAXV];
-                    /* background at this face: the z face k+1/2, or the
-                       plane's centre value for x and y faces */
-                    double rb, pb;
-                    if (d == 2) { rb = bg_rho_face(p, k + 1); pb = bg_p_face(p, k + 1); }
-                    else        { rb = bg_rho_centre(p, k);   pb = bg_p_centre(p, k); }
-                    for (int q = 0; q < nv; ++q) {
-                        wl[q] = wk->Wf[((d * 2 + 1) * nv + q) * np + c];
-                        wr[q] = wk->Wf[((d * 2 + 0) * nv + q) * np + cn];
-                    }
-                    /* reflecting wall: the far side of the wall face is the
-                       mirror image of the interior cell's predicted face
-                       state (normal velocity negated), so no mass crosses it */
-                    int cd = d == 0 ? i : (d == 1 ? j : kk);
-                    if (cd == g->ng[d] - 1 && p->bc_lo[d] == BC_REFLECT) {
-                        for (int q = 0; q < nv; ++q) wl[q] = wr[q];
-                        wl[1 + d] = -wr[1 + d];
-                    }
-                    if (cd == g->ng[d] + g->n[d] - 1 && p->bc_hi[d] == BC_REFLECT) {
-                        for (int q = 0; q < nv; ++q) wr[q] = wl[q];
-                        wr[1 + d] = -wl[1 + d];
-                    }
-                    wl[0] += rb; wr[0] += rb;
-                    wl[nd + 1] += pb; wr[nd + 1] += pb;
-                    orc_hllc(nd, gam, d, wl, wr, f);
-                    f[1 + d] -= pb;   /* momentum flux carries p' */
-                    for (int q = 0; q < nv; ++q) wk->F[(d * nv + q) * np + c] = f[q];
-                }
-            }
+    /* 5. HLLC flux through the high face of each cell along d, for every
+       face of the interior; the corner transport upwind step first takes
+       fluxes from the one-dimensional states (one ring wider) and corrects
+       the states with their transverse differences */
+    if (mode == MODE_CTU) {
+        flux_pass(p, wk, wk->Wf, wk->F1, 1);
+        ctu_correct(p, wk, dt);
     }
+    flux_pass(p, wk, wk->Wf, wk->F, 0);
 
     /* 6. conservative update, density first, then momentum with
        the time-centred density in the gravity source (MUSCL-Hancock) or the
@@ -672,13 +777,14 @@ int orc_max_threads(void)
 /* One full step of the problem's integrator with the given dt. */
 static int full_step(const orc_params *p, work_t *wk, double *U, double *U0, double dt)
 {
-    if (p->scheme == SCHEME_HANCOCK) return step_with(p, wk, U, dt, 1);
+    if (p->scheme == SCHEME_HANCOCK) return step_with(p, wk, U, dt, MODE_HANCOCK);
+    if (p->scheme == SCHEME_CTU) return step_with(p, wk, U, dt, MODE_CTU);
     /* SSP-RK2: U0 keeps U^n; U becomes U1, then U1 + dt L(U1), then the
        average with U^n */
     const long n = (long)wk->g.nvar * wk->g.n[0] * wk->g.n[1] * wk->g.n[2];
     memcpy(U0, U, sizeof(double) * n);
-    int rc1 = step_with(p, wk, U, dt, 0);   /* checks U1 */
-    step_with(p, wk, U, dt, 0);             /* U1 + dt L(U1): only its average is a state */
+    int rc1 = step_with(p, wk, U, dt, MODE_STAGE);   /* checks U1 */
+    step_with(p, wk, U, dt, MODE_STAGE);             /* U1 + dt L(U1): only its average is a state */
     for (long i = 0; i < n; ++i) U[i] = 0.5 * (U0[i] + U[i]);
     /* admissibility of U^{n+1} */
     const grid_t *g = &wk->g;

@@ -43,6 +43,7 @@ FP32 = 1
 
 HANCOCK = 0   # single-stage unsplit MUSCL-Hancock
 SSPRK2 = 1    # two-stage SSP Runge-Kutta method of lines
+CTU = 2       # corner transport upwind (Colella 1990), PLM, no background
 
 PLM = 0       # piecewise linear reconstruction, MC limiter
 PPM = 1       # piecewise parabolic reconstruction (SSPRK2, no hse)
@@ -66,7 +67,8 @@ class Problem:
     ``bg_p_f`` at the faces z_lo + f dz, f = -2 .. nz+2 (length nz + 5, entry
     f + 2).  Ghost planes need the background outside the domain.
     ``scheme`` selects the time integrator: HANCOCK (single-stage
-    MUSCL-Hancock) or SSPRK2 (two-stage method of lines); ``recon`` the
+    MUSCL-Hancock), SSPRK2 (two-stage method of lines) or CTU (corner
+    transport upwind); ``recon`` the
     reconstruction: PLM or PPM (PPM with SSPRK2 and no background only).
     """
 
