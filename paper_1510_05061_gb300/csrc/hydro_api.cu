@@ -71,7 +71,10 @@ int check_problem(const hydro_problem *p)
         return HYDRO_ERR_INVALID_ARG;
     if (p->precision != HYDRO_FP64 && p->precision != HYDRO_FP32) return HYDRO_ERR_INVALID_ARG;
     if (p->hse_subtract != 0 && p->hse_subtract != 1) return HYDRO_ERR_INVALID_ARG;
-    if (p->scheme != HYDRO_SCHEME_HANCOCK && p->scheme != HYDRO_SCHEME_SSPRK2) return HYDRO_ERR_INVALID_ARG;
+    if (p->scheme != HYDRO_SCHEME_HANCOCK && p->scheme != HYDRO_SCHEME_SSPRK2 && p->scheme != HYDRO_SCHEME_CTU)
+        return HYDRO_ERR_INVALID_ARG;
+    if (p->scheme == HYDRO_SCHEME_CTU && (p->hse_subtract || p->recon != HYDRO_RECON_PLM || p->ndim != 2))
+        return HYDRO_ERR_INVALID_ARG;
     if (p->recon != HYDRO_RECON_PLM && p->recon != HYDRO_RECON_PPM) return HYDRO_ERR_INVALID_ARG;
     if (p->recon == HYDRO_RECON_PPM) {
         // three-cell halo: every active axis needs three cells to map into
@@ -197,6 +200,8 @@ cudaError_t launch_kernel(hydro_sim *s, const StepArgs &a, int stage)
     const bool hse = s->prob.hse_subtract != 0;
     s->launches += 1;
     const int recon = s->prob.recon;
+    if (s->prob.ndim == 2 && s->prob.scheme == HYDRO_SCHEME_CTU)
+        return launch_ctu2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32);
     if (s->prob.ndim == 2)
         return launch_step2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32, stage, recon);
     const dim3 grid(s->tiles_x * s->tiles_y, (s->prob.n[2] + s->zchunk - 1) / s->zchunk);
