@@ -58,6 +58,12 @@ FLOPS_PER_ZONE_2D_RK2 = 2 * 252 + 8 + 19
 # 3D stage 13 + 75 + 15 x 19 + 216 + 70 = 659, 2D 10 + 40 + 8 x 19 + 128 + 42 = 372.
 FLOPS_PER_ZONE_3D_PPM = 2 * 659 + 10 + 25
 FLOPS_PER_ZONE_2D_PPM = 2 * 372 + 8 + 19
+# Corner transport upwind, per step: primitives, slopes, three (two) one-axis
+# predictors of 35 each, face states, first-pass HLLC, the corrections of
+# both face states per axis (to conserved, two transverse differences, back:
+# 42 per state; 2D 26), final HLLC, update and CFL speed.
+FLOPS_PER_ZONE_3D_CTU = 13 + 75 + 3 * 35 + 60 + 216 + 3 * 2 * 42 + 216 + 70 + 25
+FLOPS_PER_ZONE_2D_CTU = 10 + 40 + 2 * 25 + 32 + 128 + 2 * 2 * 26 + 128 + 42 + 19
 
 TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16"}
 
@@ -91,6 +97,10 @@ CONFIGS = {
                            desc="3D Rayleigh-Taylor 256^3 FP64, SSP-RK2 method of lines with PPM face states"),
     "rt512-fp32-ppm": dict(n=512, precision=inputs.FP32, hse=0, scheme=inputs.SSPRK2, recon=inputs.PPM,
                            desc="3D Rayleigh-Taylor 512^3 FP32 (FP64 dt and reductions), SSP-RK2 with PPM"),
+    "rt256-fp64-ctu": dict(n=256, precision=inputs.FP64, hse=0, scheme=inputs.CTU,
+                           desc="3D Rayleigh-Taylor 256^3 FP64, corner transport upwind (one fused kernel per step)"),
+    "rt512-fp32-ctu": dict(n=512, precision=inputs.FP32, hse=0, scheme=inputs.CTU,
+                           desc="3D Rayleigh-Taylor 512^3 FP32 (FP64 dt and reductions), corner transport upwind"),
     "rt256-fp64-slabs4": dict(n=256, precision=inputs.FP64, hse=0, slabs=4,
                               desc="3D Rayleigh-Taylor 256^3 FP64 cut into 4 z slabs run as virtual ranks "
                                    "(depth-2 halo exchange + dt max-reduction every step)"),
@@ -667,7 +677,9 @@ def run_gpu(args):
     # per step: one kernel (MUSCL-Hancock) or the two stage kernels (SSP-RK2)
     bytes_per_zone = (5 if rk2 else 2) * prob.nvar * itemsize
     zones_per_launch = N
-    if rk2 and prob.recon == inputs.PPM:
+    if prob.scheme == inputs.CTU:
+        flops_per_zone = FLOPS_PER_ZONE_3D_CTU if prob.ndim == 3 else FLOPS_PER_ZONE_2D_CTU
+    elif rk2 and prob.recon == inputs.PPM:
         flops_per_zone = FLOPS_PER_ZONE_3D_PPM if prob.ndim == 3 else FLOPS_PER_ZONE_2D_PPM
     elif rk2:
         flops_per_zone = FLOPS_PER_ZONE_3D_RK2 if prob.ndim == 3 else FLOPS_PER_ZONE_2D_RK2
@@ -682,6 +694,9 @@ def run_gpu(args):
     rc = f", {prob.recon}" if prob.recon else ""
     knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}{rc}>" if prob.ndim == 3
                else f"step2d_kernel<{tname}, 32, 8, {st}{rc}>") for st in stages]
+    if prob.scheme == inputs.CTU:
+        knames = [f"ctu3d_kernel<{tname}, 8, {8 if itemsize == 4 else 4}, 4>" if prob.ndim == 3
+                  else f"ctu2d_kernel<{tname}, 32, 8>"]
     kname = " + ".join(knames)
     # DRAM bytes of one step: the sum over its kernels (null if any is missing or stale)
     traffic = args.traffic

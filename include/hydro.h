@@ -75,7 +75,7 @@ enum { HYDRO_SCHEME_HANCOCK = 0, HYDRO_SCHEME_SSPRK2 = 1, HYDRO_SCHEME_CTU = 2 }
 /* CTU: the unsplit corner transport upwind method (Colella 1990): per axis a
    one-dimensional MUSCL-Hancock predictor, first-pass HLLC fluxes, face
    states corrected by the transverse flux differences, final HLLC fluxes;
-   one kernel per step.  PLM, hse_subtract = 0, ndim = 2 on the GPU. */
+   one kernel per step.  PLM and hse_subtract = 0 only. */
 /* Face-state reconstruction.  PLM: MC-limited piecewise linear (van Leer
    1977).  PPM: the piecewise parabolic method (Colella and Woodward 1984):
    interface values from the MC-limited slopes, parabola limited to be

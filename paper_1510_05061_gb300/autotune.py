@@ -116,7 +116,7 @@ def sim_signature(sim) -> str:
 
     p = sim.prob
     prec = "fp32" if p.precision == inputs.FP32 else "fp64"
-    scheme = "rk2" if getattr(p, "scheme", 0) == inputs.SSPRK2 else "hancock"
+    scheme = {inputs.SSPRK2: "rk2", inputs.CTU: "ctu"}.get(getattr(p, "scheme", 0), "hancock")
     if getattr(p, "recon", 0) == inputs.PPM:
         scheme += "-ppm"
     return (f"{torch.cuda.get_device_name()}|single|{prec}|hse{p.hse_subtract}|{scheme}"
@@ -143,7 +143,8 @@ def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 1
     Tuning advances the solve by the steps it times."""
     from . import hydro
 
-    if sim.prob.ndim != 3:
+    if sim.prob.ndim != 3 or getattr(sim.prob, "scheme", 0) == inputs.CTU:
+        # the 2D step and the corner transport upwind step have one launch shape
         return {"variant": 0, "tile": [32, 8], "zchunk": 1, "cached": False, "table": []}
     key = sim_signature(sim)
     cache = _load_cache() if use_cache else {}

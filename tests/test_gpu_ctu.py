@@ -118,6 +118,54 @@ def test_ctu_conserves_on_periodic_grid(hy):
         assert abs(T1[q] - T0[q]) <= 1e-13 * scale, q
 
 
+@pytest.mark.parametrize("bcl,bch,g", [
+    ((BC_OUTFLOW, BC_PERIODIC, BC_REFLECT), (BC_REFLECT, BC_PERIODIC, BC_REFLECT), (0.0, 0.0, -1.0)),
+    ((BC_PERIODIC, BC_REFLECT, BC_OUTFLOW), (BC_PERIODIC, BC_OUTFLOW, BC_OUTFLOW), (0.2, -0.3, 0.5)),
+    ((BC_PERIODIC,) * 3, (BC_PERIODIC,) * 3, (0.0, 0.0, 0.0)),
+])
+def test_ctu_3d_ragged(hy, orc, bcl, bch, g):
+    prob = ctu(Problem(ndim=3, n=(37, 29, 23), hi=(1.0, 0.8, 0.6), bc_lo=bcl, bc_hi=bch, grav=g))
+    W = smooth_random(prob, 23)
+    gr = gpu(hy, prob, W, steps=15)
+    o = ref(orc, prob, W, steps=15)
+    assert gr["launches"] == 15
+    assert_parity(gr["U"], o["U"], label=f"ctu 3d {bcl} {bch}")
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (5, 3, 7), (33, 9, 3), (9, 17, 5)])
+def test_ctu_3d_tiny_and_odd_grids(hy, orc, shape):
+    prob = ctu(Problem(ndim=3, n=shape, bc_lo=(BC_REFLECT, BC_PERIODIC, BC_OUTFLOW),
+                       bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_REFLECT), grav=(0.0, 0.1, -0.4)))
+    W = smooth_random(prob, 5, jump=False)
+    gr = gpu(hy, prob, W, steps=6)
+    o = ref(orc, prob, W, steps=6)
+    assert_parity(gr["U"], o["U"], label=str(shape))
+
+
+def test_ctu_3d_rayleigh_taylor_and_fp32(hy, orc):
+    prob, W = inputs.rayleigh_taylor(24, nz=40, amplitude=0.05)
+    prob = ctu(prob)
+    gr = gpu(hy, prob, W, steps=20)
+    o = ref(orc, prob, W, steps=20)
+    assert_parity(gr["U"], o["U"], label="ctu rt")
+    np.testing.assert_allclose(gr["t"], o["t"], rtol=1e-12)
+    g32 = gpu(hy, prob.replace(precision=inputs.FP32), W, steps=20)
+    assert l1rel(g32["U"][0], o["U"][0]) <= 1e-5
+
+
+def test_ctu_3d_conserves_on_periodic_grid(hy):
+    prob, W = inputs.kelvin_helmholtz(24, ndim=3, U=1.5, ratio=3.0, precision=inputs.FP64)
+    sim = hy.Simulation(ctu(prob), W)
+    T0, U0 = sim.totals(), sim.conserved()
+    sim.run_steps(50)
+    T1 = sim.totals()
+    dV = np.prod(prob.dx())
+    mom_scale = np.abs(U0[1:4]).sum() * dV
+    for q in range(5):
+        scale = mom_scale if 1 <= q <= 3 else np.abs(U0[q]).sum() * dV
+        assert abs(T1[q] - T0[q]) <= 1e-13 * scale, q
+
+
 def test_ctu_rejected_combinations(hy):
     prt, Wrt = inputs.rayleigh_taylor(8, nz=8, hse_subtract=1)
     with pytest.raises(hy.HydroError):
