@@ -65,7 +65,8 @@ FLOPS_PER_ZONE_2D_PPM = 2 * 372 + 8 + 19
 FLOPS_PER_ZONE_3D_CTU = 13 + 75 + 3 * 35 + 60 + 216 + 3 * 2 * 42 + 216 + 70 + 25
 FLOPS_PER_ZONE_2D_CTU = 10 + 40 + 2 * 25 + 32 + 128 + 2 * 2 * 26 + 128 + 42 + 19
 
-TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16"}
+# tile shape of each 3D variant; variants 4..7 stage the next plane asynchronously
+TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16", 4: "32, 8", 5: "32, 4", 6: "16, 16", 7: "32, 16"}
 
 CONFIGS = {
     # name: (builder, description, precision, hse)
@@ -434,7 +435,7 @@ def run_gpu_batch(args):
     achieved = 2 * 5 * 4 * cells / (per_launch_ms * 1e-3) / 1e9
     items3, items2, grid3, grid2 = b.items()
     b.close()
-    kname = f"step3d_batch_kernel<float, 0, {TILE_NAMES[tune['variant']]}>"
+    kname = f"step3d_batch_kernel<float, 0, {TILE_NAMES[tune['variant']]}, {int(tune['variant'] >= 4)}>"
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -688,12 +689,16 @@ def run_gpu(args):
     achieved_gbs = bytes_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e9
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
-    tile = TILE_NAMES.get(tune["variant"] if tune else 0, "32, 8") if prob.ndim == 3 else "32, 8"
+    variant = tune["variant"] if tune else (0 if itemsize == 4 else 4)
+    tile = TILE_NAMES.get(variant, "32, 8") if prob.ndim == 3 else "32, 8"
     tname = "double" if itemsize == 8 else "float"
     stages = (1, 2) if rk2 else (0,)
-    rc = f", {prob.recon}" if prob.recon else ""
-    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}{rc}>" if prob.ndim == 3
-               else f"step2d_kernel<{tname}, 32, 8, {st}{rc}>") for st in stages]
+    # template arguments as the profiler prints them: stage, reconstruction,
+    # staging depth (the tuned one for the MUSCL-Hancock step, the
+    # precision's default for the stages)
+    async_flag = int(variant >= 4) if not rk2 else int(itemsize == 8)
+    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}>"
+               if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
     if prob.scheme == inputs.CTU:
         knames = [f"ctu3d_kernel<{tname}, 8, {8 if itemsize == 4 else 4}, 4>" if prob.ndim == 3
                   else f"ctu2d_kernel<{tname}, 32, 8>"]

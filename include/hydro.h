@@ -165,9 +165,12 @@ int hydro_debug_poke(hydro_sim *sim, int var, long cell, double v);
 /* Select the 3D z-chunk length (planes per CTA); 0 restores the default. */
 int hydro_set_zchunk(hydro_sim *sim, int zchunk);
 
-/* Select the 3D tile shape: variant index of hydro_batch_variant_shape
-   (0 = 32 x 8, the default).  Variant 3 (32 x 16) is FP32 only.  Results do
-   not depend on the choice. */
+/* Select the 3D tile shape and staging depth: variant index of
+   hydro_batch_variant_shape.  Variants 0..3 load each staged plane
+   synchronously, 4..7 (the same shapes) copy the next plane asynchronously
+   one plane ahead (MUSCL-Hancock step; the other integrators use the shape
+   only).  Default: 32 x 8, variant 0 for FP32 and 4 for FP64.  Variants 3
+   and 7 (32 x 16) are FP32 only.  Results do not depend on the choice. */
 int hydro_set_tile(hydro_sim *sim, int variant);
 
 /* Number of kernels launched by this handle so far. */
@@ -234,9 +237,11 @@ int hydro_batch_init(const hydro_problem *probs, int count, void *const *Ua, voi
                      void *work, const double *const *W0, const double *const *bg, void *stream,
                      hydro_batch **out);
 
-/* Select the 3D tile shape (variant index, see hydro_batch_variant_shape;
-   variant 3 is FP32 only) and the z-chunk length (0 = default); rebuilds the
-   work lists and the graph.  Results do not depend on this choice. */
+/* Select the 3D tile shape and staging depth (variant index, see
+   hydro_set_tile; variants 3 and 7 are FP32 only) and the z-chunk length
+   (0 = default); rebuilds the work lists and the graph.  Results do not
+   depend on this choice.  hydro_batch_variant_shape gives a variant's tile
+   shape (tx x ty); variants v and v + 4 share it. */
 int hydro_batch_configure(hydro_batch *b, int variant, int zchunk);
 int hydro_batch_variant_shape(int variant, int *tx, int *ty);
 

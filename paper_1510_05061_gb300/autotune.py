@@ -1,6 +1,8 @@
-"""Autotuner for the batched step: picks the 3D tile shape (TX x TY) and the
-z-chunk length (planes marched per work item) for a batch by timing real
-steps with CUDA events on the batch's stream.
+"""Autotuner for the batched and single-solve 3D steps: picks the tile shape
+(TX x TY), the staging depth (synchronous loads, or the next plane copied
+asynchronously one plane ahead: variants 4..7) and the z-chunk length
+(planes marched per work item) by timing real steps with CUDA events on the
+solve's stream.
 
 The choice never changes results (every tile shape and chunk length gives
 bit-identical states); it only changes speed.  Tuning advances the batch by
@@ -99,12 +101,13 @@ def tune_batch(batch, steps: int = 4, zchunks: Iterable[int] = DEFAULT_ZCHUNKS,
                 break
             batch.step(2)                        # first launch of this kernel, warm caches
             ms = time_steps(batch, steps)
-            table.append({"variant": v, "tile": list(shapes[v]), "zchunk": z, "ms_per_step": ms})
+            table.append({"variant": v, "tile": list(shapes[v]), "async_staging": v >= 4, "zchunk": z,
+                          "ms_per_step": ms})
             if best is None or ms < best["ms_per_step"]:
                 best = table[-1]
     batch.configure(best["variant"], best["zchunk"])
-    choice = {"variant": best["variant"], "tile": best["tile"], "zchunk": best["zchunk"],
-              "ms_per_step": best["ms_per_step"], "table": table}
+    choice = {"variant": best["variant"], "tile": best["tile"], "async_staging": best["async_staging"],
+              "zchunk": best["zchunk"], "ms_per_step": best["ms_per_step"], "table": table}
     if use_cache:
         cache[key] = choice
         _store_cache(cache)
@@ -165,12 +168,13 @@ def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 1
                 break
             sim.run_steps(2)
             ms = time_sim_steps(sim, steps)
-            table.append({"variant": v, "tile": list(shapes[v]), "zchunk": z, "ms_per_step": ms})
+            table.append({"variant": v, "tile": list(shapes[v]), "async_staging": v >= 4, "zchunk": z,
+                          "ms_per_step": ms})
             if best is None or ms < best["ms_per_step"]:
                 best = table[-1]
     sim.configure(best["variant"], best["zchunk"])
-    choice = {"variant": best["variant"], "tile": best["tile"], "zchunk": best["zchunk"],
-              "ms_per_step": best["ms_per_step"], "table": table}
+    choice = {"variant": best["variant"], "tile": best["tile"], "async_staging": best["async_staging"],
+              "zchunk": best["zchunk"], "ms_per_step": best["ms_per_step"], "table": table}
     if use_cache:
         cache[key] = choice
         _store_cache(cache)

@@ -31,13 +31,14 @@ cudaError_t prepare(K kernel, size_t smem, int threads, int *max_grid)
     return cudaSuccess;
 }
 
-template <typename T, bool HSE, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY, bool AS>
 struct Batch3D {
     static int &grid_cap() { static int g = 0; return g; }
     static cudaError_t ensure()
     {
         if (grid_cap()) return cudaSuccess;
-        return prepare(step3d_batch_kernel<T, HSE, TX, TY>, Step3DSmem<T, HSE, TX, TY>::bytes, TX * TY,
+        return prepare(step3d_batch_kernel<T, HSE, TX, TY, AS>, Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes,
+                       TX * TY,
                        &grid_cap());
     }
     static cudaError_t launch(const BatchInst *insts, const BatchItem *items, int nitems, int parity,
@@ -45,8 +46,8 @@ struct Batch3D {
     {
         cudaError_t e = ensure();
         if (e != cudaSuccess) return e;
-        step3d_batch_kernel<T, HSE, TX, TY>
-            <<<grid, TX * TY, Step3DSmem<T, HSE, TX, TY>::bytes, s>>>(insts, items, nitems, parity);
+        step3d_batch_kernel<T, HSE, TX, TY, AS>
+            <<<grid, TX * TY, Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes, s>>>(insts, items, nitems, parity);
         return cudaGetLastError();
     }
     static int max_grid() { return ensure() == cudaSuccess ? grid_cap() : 0; }
@@ -57,9 +58,12 @@ cudaError_t launch_v(int v, const BatchInst *insts, const BatchItem *items, int 
                      int grid, cudaStream_t s)
 {
     switch (v) {
-    case 0: return Batch3D<double, HSE, 32, 8>::launch(insts, items, nitems, parity, grid, s);
-    case 1: return Batch3D<double, HSE, 32, 4>::launch(insts, items, nitems, parity, grid, s);
-    case 2: return Batch3D<double, HSE, 16, 16>::launch(insts, items, nitems, parity, grid, s);
+    case 0: return Batch3D<double, HSE, 32, 8, false>::launch(insts, items, nitems, parity, grid, s);
+    case 1: return Batch3D<double, HSE, 32, 4, false>::launch(insts, items, nitems, parity, grid, s);
+    case 2: return Batch3D<double, HSE, 16, 16, false>::launch(insts, items, nitems, parity, grid, s);
+    case 4: return Batch3D<double, HSE, 32, 8, true>::launch(insts, items, nitems, parity, grid, s);
+    case 5: return Batch3D<double, HSE, 32, 4, true>::launch(insts, items, nitems, parity, grid, s);
+    case 6: return Batch3D<double, HSE, 16, 16, true>::launch(insts, items, nitems, parity, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -68,9 +72,12 @@ template <bool HSE>
 int grid_v(int v)
 {
     switch (v) {
-    case 0: return Batch3D<double, HSE, 32, 8>::max_grid();
-    case 1: return Batch3D<double, HSE, 32, 4>::max_grid();
-    case 2: return Batch3D<double, HSE, 16, 16>::max_grid();
+    case 0: return Batch3D<double, HSE, 32, 8, false>::max_grid();
+    case 1: return Batch3D<double, HSE, 32, 4, false>::max_grid();
+    case 2: return Batch3D<double, HSE, 16, 16, false>::max_grid();
+    case 4: return Batch3D<double, HSE, 32, 8, true>::max_grid();
+    case 5: return Batch3D<double, HSE, 32, 4, true>::max_grid();
+    case 6: return Batch3D<double, HSE, 16, 16, true>::max_grid();
     default: return 0;
     }
 }

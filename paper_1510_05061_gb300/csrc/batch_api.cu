@@ -416,6 +416,7 @@ int hydro_batch_create(int max_instances, long max_items3d, long max_items2d, in
         return HYDRO_ERR_INVALID_ARG;
     hydro_batch *b = new (std::nothrow) hydro_batch();
     if (!b) return HYDRO_ERR_OOM;
+    b->variant = precision == HYDRO_FP32 ? 0 : 4;   // 32 x 8; FP64 stages asynchronously
     b->max_instances = max_instances;
     b->cap3 = max_items3d;
     b->cap2 = max_items2d;

@@ -333,9 +333,10 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
         s->tiles_x = tiles_along(prob->n[0], STEP2D_TX);
         s->tiles_y = tiles_along(prob->n[1], STEP2D_TY);
     } else {
-        s->variant = 0;
-        s->tiles_x = tiles_along(prob->n[0], TILE3D_SHAPES[0].tx);
-        s->tiles_y = tiles_along(prob->n[1], TILE3D_SHAPES[0].ty);
+        // 32 x 8 tiles; FP64 stages asynchronously (variant 4)
+        s->variant = prob->precision == HYDRO_FP32 ? 0 : 4;
+        s->tiles_x = tiles_along(prob->n[0], TILE3D_SHAPES[s->variant].tx);
+        s->tiles_y = tiles_along(prob->n[1], TILE3D_SHAPES[s->variant].ty);
     }
     s->zchunk = default_zchunk(s);
 

@@ -17,9 +17,14 @@ constexpr int STEP2D_TY = 8;
 // tile is FP32 only: an FP64 thread needs about twice the 128 registers a
 // 512-thread CTA can have.
 struct TileShape { int tx, ty; };
-constexpr int TILE3D_VARIANTS = 4;
-constexpr TileShape TILE3D_SHAPES[TILE3D_VARIANTS] = {{32, 8}, {32, 4}, {16, 16}, {32, 16}};
-inline bool tile3d_available(int v, bool fp32) { return v >= 0 && v < TILE3D_VARIANTS && (v != 3 || fp32); }
+// Variants 4..7 are the shapes of 0..3 staging the next plane with
+// asynchronous copies one plane ahead (the staging depth the autotuner also
+// chooses); 0..3 load each plane synchronously.
+constexpr int TILE3D_VARIANTS = 8;
+constexpr TileShape TILE3D_SHAPES[TILE3D_VARIANTS] = {{32, 8}, {32, 4}, {16, 16}, {32, 16},
+                                                      {32, 8}, {32, 4}, {16, 16}, {32, 16}};
+inline bool tile3d_available(int v, bool fp32) { return v >= 0 && v < TILE3D_VARIANTS && (v % 4 != 3 || fp32); }
+inline bool tile3d_async(int v) { return v >= 4; }
 constexpr int BATCH2D_TX = 32, BATCH2D_TY = 8;
 
 // Persistent batched steps over a device work list; `grid` CTAs walk the

@@ -318,7 +318,7 @@ int hydro_slabs_init(const hydro_problem *global, int nranks, void *const *Ua, v
     S->bytes_per = global->precision == HYDRO_FP32 ? 4 : 8;
     S->plane = (long long)global->n[0] * global->n[1];
     S->stream = static_cast<cudaStream_t>(stream);
-    S->variant = 0;
+    S->variant = global->precision == HYDRO_FP32 ? 0 : 4;   // 32 x 8; FP64 stages asynchronously
     S->cell_volume = 1.0;
     for (int d = 0; d < 3; ++d) {
         S->dx[d] = (global->hi[d] - global->lo[d]) / global->n[d];

@@ -26,7 +26,7 @@ cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
 template <int ST, int RC, bool HSE>
 cudaError_t launch_v(int v, const StepArgs &a, dim3 grid, cudaStream_t s)
 {
-    switch (v) {
+    switch (v % 4) {   // the stages use the precision's default staging
     case 0: return launch3d<ST, RC, HSE, 32, 8>(a, grid, s);
     case 1: return launch3d<ST, RC, HSE, 32, 4>(a, grid, s);
     case 2: return launch3d<ST, RC, HSE, 16, 16>(a, grid, s);

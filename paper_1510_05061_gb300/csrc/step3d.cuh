@@ -21,13 +21,15 @@
 
 #include "hydro_device.cuh"
 
-// Build option: stage the next plane of the FP64 step with asynchronous
-// global->shared copies (cp.async) issued one plane ahead, so that its loads
-// are in flight while the current plane is computed without holding them in
-// registers.  0 keeps the synchronous loads (load, then convert).  Measured
-// on GB300: +1.4 % for FP64 (one CTA per SM); no gain for FP32, whose second
-// resident CTA already hides the load latency, so FP32 always loads
-// synchronously and keeps the shared memory.
+// Staging depth (template argument AS): with AS the next plane is staged by
+// asynchronous global->shared copies (cp.async) issued one plane ahead, so
+// that its loads are in flight while the current plane is computed without
+// holding them in registers; without it each plane is loaded, then
+// converted.  The MUSCL-Hancock step offers both (tile variants 4..7 and
+// 0..3) to the autotuner; the other kernels take the precision's default:
+// asynchronous for FP64 (+1.4 % measured on GB300, one CTA per SM), none for
+// FP32 (its further resident CTAs already hide the loads).  The build option
+// HYDRO_ASYNC_STAGING=0 turns the asynchronous path off everywhere.
 #ifndef HYDRO_ASYNC_STAGING
 #define HYDRO_ASYNC_STAGING 1
 #endif
@@ -52,7 +54,7 @@
 
 namespace hydro {
 
-template <typename T, bool HSE, int TX, int TY, int RC = RECON_PLM>
+template <typename T, bool HSE, int TX, int TY, int RC = RECON_PLM, bool AS = (sizeof(T) == 8)>
 struct Step3DSmem {
     static constexpr int NV = 5;
     // halo depth and primitive ring: PLM needs cells i-2..i+2 for the faces
@@ -70,7 +72,7 @@ struct Step3DSmem {
     static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
     static constexpr size_t fy = (size_t)NV * (TY + 1) * TX;   // [NV][TY+1][TX]
     // conserved values of the next two planes as copied from HBM
-    static constexpr bool async = HYDRO_ASYNC_STAGING != 0 && sizeof(T) == 8;
+    static constexpr bool async = HYDRO_ASYNC_STAGING != 0 && AS;
     static constexpr size_t raw = async ? 2ull * NV * HX * HY : 0;   // [2][NV][HY*HX]
     static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy + raw;
     static constexpr size_t bytes = elems * sizeof(T);
@@ -120,13 +122,14 @@ __device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chu
 // take the gravity source on the momentum from the stage's own density.
 // RC selects the face states: MC-limited linear (RECON_PLM), or piecewise
 // parabolic (RECON_PPM, Runge-Kutta stages without background only).
-template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
+template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM,
+          bool AS = (sizeof(T) == 8)>
 __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chunk, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
     static_assert(RC == RECON_PLM || (ST != STAGE_HANCOCK && !HSE), "PPM: method-of-lines stages, no background");
-    using S = Step3DSmem<T, HSE, TX, TY, RC>;
+    using S = Step3DSmem<T, HSE, TX, TY, RC, AS>;
     constexpr bool ASYNC = S::async;
     constexpr int HX = S::HX, HY = S::HY, H = S::H, NR = S::NR;
     // planes staged ahead of the plane whose face states are computed
@@ -612,7 +615,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
 }
 
-template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM>
+template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM,
+          bool AS = (sizeof(T) == 8)>
 __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) step3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
@@ -634,7 +638,7 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    step3d_body<T, HSE, TX, TY, ST, RC>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    step3d_body<T, HSE, TX, TY, ST, RC, AS>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
         // the intermediate state only raises error bits; dt and time move
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
 // instances (item it goes to CTA it mod gridDim.x).  Each instance keeps its
 // own time-control block; the CTA that completes the instance's last item
 // sets that instance's next dt (per-instance CFL).
-template <typename T, bool HSE, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY, bool AS = (sizeof(T) == 8)>
 __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY))
 step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
                     int nitems, int parity)
@@ -676,7 +680,8 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
             const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
             T smax;
             bool bad;
-            step3d_body<T, HSE, TX, TY>(sa, w.tile, w.chunk, dtd, smem_raw, smax, bad);
+            step3d_body<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS>(sa, w.tile, w.chunk, dtd, smem_raw, smax,
+                                                                      bad);
             const bool bad_cta = __syncthreads_or(bad) != 0;
             const double m = block_max_t<NT, T>(smax, red);
             finish_step<NT>(m, bad_cta, sa, insts[w.inst].nitems, w.local, dtd, true, &s_last);

@@ -1,5 +1,6 @@
 // step3d_f32.cu -- FP32 instantiations of the fused single-solve 3D step
-// for every tile shape.
+// for every tile shape and
+// staging depth.
 #include "launchers.h"
 #include "step3d.cuh"
 
@@ -7,11 +8,11 @@ namespace hydro {
 
 namespace {
 
-template <typename T, bool HSE, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY, bool AS>
 cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
-    auto k = step3d_kernel<T, HSE, TX, TY>;
-    constexpr size_t smem = Step3DSmem<T, HSE, TX, TY>::bytes;
+    auto k = step3d_kernel<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS>;
+    constexpr size_t smem = Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes;
     static bool configured = false;   // the attribute is per function
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -26,10 +27,14 @@ template <bool HSE>
 cudaError_t launch_v(int v, const StepArgs &a, dim3 grid, cudaStream_t s)
 {
     switch (v) {
-    case 0: return launch3d<float, HSE, 32, 8>(a, grid, s);
-    case 1: return launch3d<float, HSE, 32, 4>(a, grid, s);
-    case 2: return launch3d<float, HSE, 16, 16>(a, grid, s);
-    case 3: return launch3d<float, HSE, 32, 16>(a, grid, s);
+    case 0: return launch3d<float, HSE, 32, 8, false>(a, grid, s);
+    case 1: return launch3d<float, HSE, 32, 4, false>(a, grid, s);
+    case 2: return launch3d<float, HSE, 16, 16, false>(a, grid, s);
+    case 3: return launch3d<float, HSE, 32, 16, false>(a, grid, s);
+    case 4: return launch3d<float, HSE, 32, 8, true>(a, grid, s);
+    case 5: return launch3d<float, HSE, 32, 4, true>(a, grid, s);
+    case 6: return launch3d<float, HSE, 16, 16, true>(a, grid, s);
+    case 7: return launch3d<float, HSE, 32, 16, true>(a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

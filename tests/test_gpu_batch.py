@@ -48,7 +48,7 @@ def batch_state(hy, b, i):
     return b.get_state(i)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 4, 6])
 def test_mixed_batch_equals_solo_bitwise(hy, variant):
     items = mixed_fp64()
     steps = 9

@@ -345,7 +345,7 @@ def test_fp32_rt_linear_phase_density_error(hy):
     assert err <= 1e-3, err
 
 
-@pytest.mark.parametrize("prec,variants", [(inputs.FP64, (0, 1, 2)), (inputs.FP32, (0, 1, 2, 3))])
+@pytest.mark.parametrize("prec,variants", [(inputs.FP64, (0, 1, 2, 4, 5, 6)), (inputs.FP32, (0, 1, 2, 3, 4, 5, 6, 7))])
 def test_tile_shape_invariance_bitwise(hy, prec, variants):
     """Every tile shape the autotuner may pick gives the same bits (ragged
     sizes, reflecting walls, hydrostatic mode)."""
