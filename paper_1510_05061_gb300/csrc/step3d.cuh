@@ -496,20 +496,37 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             // the low face of this cell is a wall when it sits on the domain's
             // low boundary, or on the high boundary (ragged tile: the cell is
             // the first one past the domain)
-            const bool xw_lo = x0 + tx == 0 && a.bc_lo[0] == BC_REFLECT;
-            const bool xw_hi = x0 + tx == nx && a.bc_hi[0] == BC_REFLECT;
-            const bool yw_lo = y0 + ty == 0 && a.bc_lo[1] == BC_REFLECT;
-            const bool yw_hi = y0 + ty == ny && a.bc_hi[1] == BC_REFLECT;
+            // a tile away from every reflecting wall (the common case, the
+            // same for the whole CTA) takes the states without the selects
+            const bool wall_tile = (a.bc_lo[0] == BC_REFLECT && x0 == 0) || (a.bc_hi[0] == BC_REFLECT && x0 + TX >= nx)
+                                || (a.bc_lo[1] == BC_REFLECT && y0 == 0) || (a.bc_hi[1] == BC_REFLECT && y0 + TY >= ny)
+                                || wall_zlo || wall_zhi;
+            if (!wall_tile) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const T xl = WX(wxh, q, ty, tx - 1), xr = WX(wxl, q, ty, tx);
-                wlx[q] = xw_lo ? (q == 1 ? -xr : xr) : xl;
-                wrx[q] = xw_hi ? (q == 1 ? -xl : xl) : xr;
-                const T yl = WY(wyh, q, ty - 1, tx), yr = WY(wyl, q, ty, tx);
-                wly[q] = yw_lo ? (q == 2 ? -yr : yr) : yl;
-                wry[q] = yw_hi ? (q == 2 ? -yl : yl) : yr;
+                for (int q = 0; q < NV; ++q) {
+                    wlx[q] = WX(wxh, q, ty, tx - 1);
+                    wrx[q] = WX(wxl, q, ty, tx);
+                    wly[q] = WY(wyh, q, ty - 1, tx);
+                    wry[q] = WY(wyl, q, ty, tx);
+                    wlz[q] = ztop_prev[q];
+                    wrz[q] = zlo[q];
+                }
+            } else {
+                const bool xw_lo = x0 + tx == 0 && a.bc_lo[0] == BC_REFLECT;
+                const bool xw_hi = x0 + tx == nx && a.bc_hi[0] == BC_REFLECT;
+                const bool yw_lo = y0 + ty == 0 && a.bc_lo[1] == BC_REFLECT;
+                const bool yw_hi = y0 + ty == ny && a.bc_hi[1] == BC_REFLECT;
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    const T xl = WX(wxh, q, ty, tx - 1), xr = WX(wxl, q, ty, tx);
+                    wlx[q] = xw_lo ? (q == 1 ? -xr : xr) : xl;
+                    wrx[q] = xw_hi ? (q == 1 ? -xl : xl) : xr;
+                    const T yl = WY(wyh, q, ty - 1, tx), yr = WY(wyl, q, ty, tx);
+                    wly[q] = yw_lo ? (q == 2 ? -yr : yr) : yl;
+                    wry[q] = yw_hi ? (q == 2 ? -yl : yl) : yr;
+                }
+                z_states(wlz, wrz);
             }
-            z_states(wlz, wrz);
             hllc<T, ND, 0, HSE>(wlx, wrx, rb_c, pb_c, gam, igm1, fxv);
             hllc<T, ND, 1, HSE>(wly, wry, rb_c, pb_c, gam, igm1, fyv);
             hllc<T, ND, 2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
