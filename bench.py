@@ -700,7 +700,7 @@ def run_gpu(args):
     knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}>"
                if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
     if prob.scheme == inputs.CTU:
-        knames = [f"ctu3d_kernel<{tname}, 8, {8 if itemsize == 4 else 4}, 4>" if prob.ndim == 3
+        knames = [f"ctu3d_kernel<{tname}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3
                   else f"ctu2d_kernel<{tname}, 32, 8>"]
     kname = " + ".join(knames)
     # DRAM bytes of one step: the sum over its kernels (null if any is missing or stale)

@@ -1,36 +1,58 @@
 // ctu3d.cu -- FP64 and FP32 instantiations of the fused 3D corner transport
-// upwind step.  Blocks: FP32 8 x 8 x 4 cells (256 threads, 127 KB of shared
-// memory), FP64 8 x 4 x 4 (128 threads, 154 KB).
+// upwind step.  Tiles: FP32 16 x 16 (256 threads, 152 KB of shared memory),
+// FP64 16 x 8 (128 threads, 171 KB); z-chunks sized for several waves of
+// the 152 SMs (one CTA per SM).
+#include <algorithm>
+
 #include "ctu3d.cuh"
 #include "launchers.h"
 
 namespace hydro {
 
-template <typename T, int TX, int TY, int TZ>
-static cudaError_t launch_ctu(const StepArgs &a, cudaStream_t s)
+namespace {
+
+constexpr int CTU_TX = 16;
+int ctu_ty(bool fp32) { return fp32 ? 16 : 8; }
+
+// planes per CTA: at least 8 waves of one CTA per SM, chunks of 8 or more
+int ctu_zchunk(const int n[3], bool fp32)
 {
-    auto k = ctu3d_kernel<T, TX, TY, TZ>;
-    constexpr size_t smem = Ctu3DSmem<T, TX, TY, TZ>::bytes;
+    const long long tiles = (long long)((n[0] + CTU_TX - 1) / CTU_TX) * ((n[1] + ctu_ty(fp32) - 1) / ctu_ty(fp32));
+    long long nch = (8ll * 152 + tiles - 1) / tiles;
+    nch = std::min(nch, std::max(1ll, (long long)(n[2] / 8)));
+    return (int)((n[2] + nch - 1) / nch);
+}
+
+template <typename T, int TX, int TY>
+cudaError_t launch_ctu(const StepArgs &a0, cudaStream_t s)
+{
+    auto k = ctu3d_kernel<T, TX, TY>;
+    constexpr size_t smem = Ctu3DSmem<T, TX, TY>::bytes;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const long long blocks = (long long)((a.n[0] + TX - 1) / TX) * ((a.n[1] + TY - 1) / TY) * ((a.n[2] + TZ - 1) / TZ);
-    k<<<(unsigned)blocks, TX * TY * TZ, smem, s>>>(a);
+    StepArgs a = a0;
+    a.tiles_x = (a.n[0] + TX - 1) / TX;
+    a.zchunk = ctu_zchunk(a.n, sizeof(T) == 4);
+    const dim3 grid(a.tiles_x * ((a.n[1] + TY - 1) / TY), (a.n[2] + a.zchunk - 1) / a.zchunk);
+    k<<<grid, TX * TY, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+}  // namespace
+
 long long ctu3d_blocks(const int n[3], bool fp32)
 {
-    const int tx = 8, ty = fp32 ? 8 : 4, tz = 4;
-    return (long long)((n[0] + tx - 1) / tx) * ((n[1] + ty - 1) / ty) * ((n[2] + tz - 1) / tz);
+    // upper bound over chunk lengths (at least one plane per chunk)
+    return (long long)((n[0] + CTU_TX - 1) / CTU_TX) * ((n[1] + ctu_ty(fp32) - 1) / ctu_ty(fp32)) * n[2];
 }
 
 cudaError_t launch_ctu3d(const StepArgs &a, cudaStream_t s, bool fp32)
 {
-    return fp32 ? launch_ctu<float, 8, 8, 4>(a, s) : launch_ctu<double, 8, 4, 4>(a, s);
+    return fp32 ? launch_ctu<float, 16, 16>(a, s) : launch_ctu<double, 16, 8>(a, s);
 }
 
 }  // namespace hydro
