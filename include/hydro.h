@@ -169,12 +169,23 @@ int hydro_set_zchunk(hydro_sim *sim, int zchunk);
    hydro_batch_variant_shape.  Variants 0..3 load each staged plane
    synchronously, 4..7 (the same shapes) copy the next plane asynchronously
    one plane ahead (MUSCL-Hancock step; the other integrators use the shape
-   only).  Default: 32 x 8, variant 0 for FP32 and 4 for FP64.  Variants 3
+   only).  Default: variant 7 (32 x 16) for FP32, 6 (16 x 16) for FP64, the
+   autotuner's usual choices on GB300.  Variants 3
    and 7 (32 x 16) are FP32 only.  Results do not depend on the choice. */
 int hydro_set_tile(hydro_sim *sim, int variant);
 
 /* Number of kernels launched by this handle so far. */
 long hydro_launch_count(hydro_sim *sim);
+
+/* Checkpoint to / restart from a file: a header (magic "HYDROCK1", version
+   1, the problem, t, step, state size, FNV-1a checksum of the state) and
+   the raw stored state (hydro_get_state's layout).  Load needs a handle
+   made with the same problem (and background tables); it rejects any
+   mismatch, short or corrupted file with HYDRO_ERR_INVALID_ARG and leaves
+   the handle unchanged, else sets state, t and step as hydro_set_state.
+   Both synchronise the handle's stream. */
+int hydro_checkpoint_save(hydro_sim *sim, const char *path);
+int hydro_checkpoint_load(hydro_sim *sim, const char *path);
 
 /* Test hook: evaluate the update's FP64 arithmetic helpers on n device
    values, out[i] = 1/x[i] (which = 0), y[i]/x[i] (1), 1/sqrt(x[i]) (2) or

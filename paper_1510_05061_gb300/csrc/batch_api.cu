@@ -5,6 +5,7 @@
 // continuous-batching server uses that); the work lists and the graph are
 // rebuilt lazily when membership or configuration changes.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -416,7 +417,7 @@ int hydro_batch_create(int max_instances, long max_items3d, long max_items2d, in
         return HYDRO_ERR_INVALID_ARG;
     hydro_batch *b = new (std::nothrow) hydro_batch();
     if (!b) return HYDRO_ERR_OOM;
-    b->variant = precision == HYDRO_FP32 ? 0 : 4;   // 32 x 8; FP64 stages asynchronously
+    b->variant = precision == HYDRO_FP32 ? 7 : 6;   // asynchronous staging, 32 x 16 (FP32) / 16 x 16 (FP64)
     b->max_instances = max_instances;
     b->cap3 = max_items3d;
     b->cap2 = max_items2d;
@@ -523,6 +524,8 @@ int hydro_batch_variant_shape(int variant, int *tx, int *ty)
 
 int hydro_batch_step(hydro_batch *b, long nsteps)
 {
+    nvtxRangePushA("hydro_batch_step");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     if (!b || nsteps < 0) return HYDRO_ERR_INVALID_ARG;
     if (b->dirty) {
         int rc = rebuild(b);

@@ -15,6 +15,7 @@
 // Given the same data and dt, every slab computes exactly the cells the
 // undivided solve computes.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -318,7 +319,7 @@ int hydro_slabs_init(const hydro_problem *global, int nranks, void *const *Ua, v
     S->bytes_per = global->precision == HYDRO_FP32 ? 4 : 8;
     S->plane = (long long)global->n[0] * global->n[1];
     S->stream = static_cast<cudaStream_t>(stream);
-    S->variant = global->precision == HYDRO_FP32 ? 0 : 4;   // 32 x 8; FP64 stages asynchronously
+    S->variant = global->precision == HYDRO_FP32 ? 7 : 6;   // asynchronous staging, 32 x 16 / 16 x 16
     S->cell_volume = 1.0;
     for (int d = 0; d < 3; ++d) {
         S->dx[d] = (global->hi[d] - global->lo[d]) / global->n[d];
@@ -348,8 +349,8 @@ int hydro_slabs_init(const hydro_problem *global, int nranks, void *const *Ua, v
         ctrls[r] = sl.ctrl;
         sl.bc_lo = (r == 0 && !per) ? global->bc_lo[2] : BC_HALO;
         sl.bc_hi = (r == nranks - 1 && !per) ? global->bc_hi[2] : BC_HALO;
-        sl.tiles_x = tiles_along(global->n[0], TILE3D_SHAPES[0].tx);
-        sl.tiles_y = tiles_along(global->n[1], TILE3D_SHAPES[0].ty);
+        sl.tiles_x = tiles_along(global->n[0], TILE3D_SHAPES[S->variant].tx);
+        sl.tiles_y = tiles_along(global->n[1], TILE3D_SHAPES[S->variant].ty);
         e = cudaMemsetAsync(w, 0, L.total, S->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(Ua[r], 0, hydro_slab_state_bytes(global, nranks, r), S->stream);
         if (e == cudaSuccess && global->hse_subtract) {
@@ -418,6 +419,8 @@ int hydro_slabs_init(const hydro_problem *global, int nranks, void *const *Ua, v
 
 int hydro_slabs_step(hydro_slabs *S, long nsteps)
 {
+    nvtxRangePushA("hydro_slabs_step");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     if (!S || nsteps < 0) return HYDRO_ERR_INVALID_ARG;
     const bool fp32 = S->g.precision == HYDRO_FP32;
     for (long i = 0; i < nsteps; ++i) {

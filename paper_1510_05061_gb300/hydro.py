@@ -50,7 +50,7 @@ EXPORTS = (
     "hydro_batch_create", "hydro_batch_add", "hydro_batch_remove", "hydro_batch_set_graph",
     "hydro_batch_configure", "hydro_batch_variant_shape", "hydro_batch_step", "hydro_batch_reduce",
     "hydro_batch_get_fields", "hydro_batch_get_state", "hydro_batch_current", "hydro_batch_launch_count", "hydro_batch_items",
-    "hydro_batch_destroy", "hydro_slab_extent", "hydro_slab_state_bytes", "hydro_slab_workspace_bytes",
+    "hydro_batch_destroy", "hydro_checkpoint_save", "hydro_checkpoint_load", "hydro_slab_extent", "hydro_slab_state_bytes", "hydro_slab_workspace_bytes",
     "hydro_slabs_exchange_plan", "hydro_slabs_init", "hydro_slabs_configure", "hydro_slabs_step",
     "hydro_slabs_get_state", "hydro_slabs_get_fields", "hydro_slabs_reduce", "hydro_slabs_launch_count", "hydro_slabs_destroy",
 )
@@ -159,6 +159,10 @@ def load(path: str = LIB_PATH):
     L.hydro_batch_items.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
     L.hydro_batch_destroy.restype = C.c_int
     L.hydro_batch_destroy.argtypes = [vp]
+    L.hydro_checkpoint_save.restype = C.c_int
+    L.hydro_checkpoint_save.argtypes = [vp, C.c_char_p]
+    L.hydro_checkpoint_load.restype = C.c_int
+    L.hydro_checkpoint_load.argtypes = [vp, C.c_char_p]
     L.hydro_totals_noalloc.restype = C.c_int
     L.hydro_totals_noalloc.argtypes = [P, vp, D, vp, D]
     IP = C.POINTER(C.c_int)
@@ -415,6 +419,14 @@ class Simulation:
         if raw.nbytes != self.state_bytes:
             raise ValueError("state size mismatch")
         hydro_set_state(self.h, raw, t, step)
+
+    def save_checkpoint(self, path: str):
+        """State, time and step to a file (hydro_checkpoint_save)."""
+        _check(load().hydro_checkpoint_save(self.h, os.fsencode(path)), "hydro_checkpoint_save")
+
+    def load_checkpoint(self, path: str):
+        """Restart from a file written for the same problem."""
+        _check(load().hydro_checkpoint_load(self.h, os.fsencode(path)), "hydro_checkpoint_load")
 
     def current_ptr(self) -> int:
         return hydro_current(self.h)

@@ -20,6 +20,7 @@ from __future__ import annotations
 import collections
 import dataclasses
 import math
+import threading
 import time
 from typing import Callable, Dict, List, Optional
 
@@ -62,10 +63,54 @@ def make_payload(req: Request, precision: int = inputs.FP32) -> Request:
 
 
 def requests_from_inputs(count: int, rate: float, seed: int = 151005063, precision: int = inputs.FP32,
-                         **kw) -> List[Request]:
+                         lazy: bool = False, **kw) -> List[Request]:
+    """The seeded request stream; with lazy the payloads are left to the
+    server, which builds them ahead of admission on a background thread."""
     reqs = [Request(id=r["id"], arrival=r["arrival"], family=r["family"], n=r["n"], steps=r["steps"],
                     seed=r["seed"]) for r in inputs.served_requests(count=count, rate=rate, seed=seed, **kw)]
-    return [make_payload(r, precision) for r in reqs]
+    return reqs if lazy else [make_payload(r, precision) for r in reqs]
+
+
+class PayloadPrefetcher:
+    """Builds request payloads in arrival order on a background thread, at
+    most `depth` ahead of admission, so that a long request stream never
+    holds all its initial fields in host memory at once."""
+
+    def __init__(self, requests: List[Request], precision: int, depth: int = 8):
+        self._order = [r for r in sorted(requests, key=lambda r: r.arrival) if r.prob is None]
+        self.ids = {r.id for r in self._order}
+        self._precision = precision
+        self._room = threading.Semaphore(depth)
+        self._cv = threading.Condition()
+        self._ready = set()
+        self._error: Optional[BaseException] = None
+        self._thread = threading.Thread(target=self._work, daemon=True)
+        self._thread.start()
+
+    def _work(self):
+        try:
+            for r in self._order:
+                self._room.acquire()
+                make_payload(r, self._precision)
+                with self._cv:
+                    self._ready.add(r.id)
+                    self._cv.notify_all()
+        except BaseException as e:   # reported to the waiting server thread
+            with self._cv:
+                self._error = e
+                self._cv.notify_all()
+
+    def wait(self, req: Request):
+        with self._cv:
+            while req.id not in self._ready and self._error is None:
+                self._cv.wait()
+            if self._error is not None and req.id not in self._ready:
+                raise RuntimeError("payload generation failed") from self._error
+
+    def release(self, req: Request):
+        """The request's fields are on the device: free them and make room."""
+        req.W = None
+        self._room.release()
 
 
 class Server:
@@ -180,13 +225,19 @@ class Server:
             time_scale: float = 1.0) -> dict:
         """Serve `requests` (arrival times scaled by time_scale) to completion."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        prefetch = PayloadPrefetcher(requests, self.precision) if any(r.prob is None for r in requests) else None
         finished: List[Request] = []
         t0 = time.perf_counter()
         while pending or self.active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival * time_scale <= now:
+                lazy = prefetch is not None and pending[0].id in prefetch.ids
+                if lazy:
+                    prefetch.wait(pending[0])
                 if not self.try_admit(pending[0], now):
                     break
+                if lazy:
+                    prefetch.release(pending[0])
                 pending.popleft()
             if not self.active:
                 if pending:

@@ -284,6 +284,35 @@ def test_checkpoint_restart_bitwise(hy):
     assert c.nstep == 12 and c.t == a.t
 
 
+def test_checkpoint_file_restart_bitwise(hy, tmp_path):
+    prob, W = inputs.rayleigh_taylor(16, nz=32, amplitude=0.05, hse_subtract=1)
+    a = hy.Simulation(prob, W)
+    a.run_steps(12)
+    ref = a.get_state()
+    b = hy.Simulation(prob, W)
+    b.run_steps(5)
+    path = str(tmp_path / "rt.ck")
+    b.save_checkpoint(path)
+    c = hy.Simulation(prob, W)
+    c.load_checkpoint(path)
+    assert c.nstep == 5 and c.t == b.t
+    c.run_steps(7)
+    assert np.array_equal(c.get_state(), ref) and c.t == a.t
+    # a handle of another problem, a truncated file and a flipped byte are refused
+    other = hy.Simulation(prob.replace(cfl=0.7), W)
+    with pytest.raises(hy.HydroError):
+        other.load_checkpoint(path)
+    raw = open(path, "rb").read()
+    open(path + ".short", "wb").write(raw[:-8])
+    bad = bytearray(raw)
+    bad[-3] ^= 0x40
+    open(path + ".bad", "wb").write(bytes(bad))
+    for p in (path + ".short", path + ".bad", str(tmp_path / "missing.ck")):
+        with pytest.raises(hy.HydroError):
+            c.load_checkpoint(p)
+    assert np.array_equal(c.get_state(), ref)      # unchanged by the refused loads
+
+
 def test_nonphysical_state_reported(hy):
     prob, W = inputs.sod(32)
     sim = hy.Simulation(prob, W)

@@ -89,3 +89,22 @@ def test_slot_limit_and_reuse(env):
     assert max(seen) <= 2 and stats["requests"] == 5
     for r in reqs:
         assert np.array_equal(r.result, solo_state(hydro, r)), r.id
+
+
+def test_lazy_payloads_match_eager(env):
+    """A stream whose payloads are built by the background prefetcher gives
+    the same results as one built up front."""
+    torch, hydro, serve = env
+    kw = dict(count=6, rate=1e6, seed=7, kh2d=(32, 48), rt3d=(16, 24), steps=(3, 5))
+    eager = serve.requests_from_inputs(**kw)
+    lazy = serve.requests_from_inputs(lazy=True, **kw)
+    assert all(r.prob is None for r in lazy)
+    out = []
+    for reqs in (eager, lazy):
+        srv = serve.Server(budget_bytes=2e9, max_active=3, max_items3d=4096, max_items2d=4096)
+        srv.run(reqs, keep_results=lambda r: True)
+        srv.close()
+        out.append({r.id: r.result for r in reqs})
+    assert all(r.W is None for r in lazy)
+    for i in out[0]:
+        assert np.array_equal(out[0][i], out[1][i])
