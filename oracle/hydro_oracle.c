@@ -35,7 +35,7 @@
  * flux divergence, momentum source g rho of the stage state and the same
  * mass-flux energy source.  dt is taken from U^n.
  *
- * Third integrator (scheme = 2, PLM and hse = 0 only): the unsplit corner
+ * Third integrator (scheme = 2, PLM only): the unsplit corner
  * transport upwind method of Colella (1990): per axis d a one-dimensional
  * MUSCL-Hancock predictor (only the axis's own A_d term, half a step of
  * gravity) gives face states; HLLC fluxes from those states at every face
@@ -44,7 +44,13 @@
  * F_e(-)) for every other axis e (kept uncorrected for a cell whose
  * corrected pair along d would have a non-positive density or pressure);
  * HLLC again on the corrected states; the update and sources of the
- * MUSCL-Hancock step.
+ * MUSCL-Hancock step.  In hydrostatic-background mode the scheme is the
+ * plain one rewritten on perturbations: the z predictor advects the
+ * background and takes g rho'/rho - B_k/rho (as the MUSCL-Hancock half step
+ * does), the x and y predictors take g; a face state is corrected as a total
+ * state (background at the face added before, removed after), and since the
+ * first-pass z fluxes carry p', the background's pressure difference across
+ * the cell is added to the z-momentum correction of x and y states.
  *
  * Second reconstruction (recon = 1, with scheme = 1 and hse = 0 only): the
  * piecewise parabolic method of Colella and Woodward (1984) in primitive
@@ -146,7 +152,7 @@ static int check_params(const orc_params *p)
     }
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0)) return ERR_ARG;
     if (p->scheme != SCHEME_HANCOCK && p->scheme != SCHEME_SSPRK2 && p->scheme != SCHEME_CTU) return ERR_ARG;
-    if (p->scheme == SCHEME_CTU && (p->hse || p->recon != RECON_PLM)) return ERR_ARG;
+    if (p->scheme == SCHEME_CTU && p->recon != RECON_PLM) return ERR_ARG;
     if (p->recon != RECON_PLM && p->recon != RECON_PPM) return ERR_ARG;
     if (p->recon == RECON_PPM) {
         if (p->scheme != SCHEME_SSPRK2 || p->hse) return ERR_ARG;
@@ -515,9 +521,16 @@ static void ctu_correct(const orc_params *p, work_t *wk, double dt)
                     long c = pidx(g, i, j, kk);
                     double wc[2][MAXV];
                     int bad = 0;
+                    /* background at the two faces: the plane's centre value for x
+                       and y faces, the face values for z faces (hse mode) */
+                    const int k = zplane(g, kk);
                     for (int s = 0; s < 2; ++s) {
+                        double rb = bg_rho_centre(p, k), pb = bg_p_centre(p, k);
+                        if (d == 2) { rb = bg_rho_face(p, k + s); pb = bg_p_face(p, k + s); }
                         double w[MAXV], u[MAXV];
                         for (int q = 0; q < nv; ++q) w[q] = wk->Wf[((d * 2 + s) * nv + q) * np + c];
+                        w[0] += rb;
+                        w[nd + 1] += pb;
                         prim_to_cons(nd, p->gamma, w, u);
                         for (int e = 0; e < nd; ++e) {
                             if (e == d) continue;
@@ -525,9 +538,15 @@ static void ctu_correct(const orc_params *p, work_t *wk, double dt)
                                 const double *Fq = wk->F1 + (e * nv + q) * np;
                                 u[q] -= dt / (2.0 * g->dx[e]) * (Fq[c] - Fq[c - st[e]]);
                             }
+                            /* hse: the z fluxes carry p'; the correction of a
+                               total state needs the background's pressure too */
+                            if (p->hse && e == 2)
+                                u[3] -= dt / (2.0 * g->dx[2]) * (bg_p_face(p, k + 1) - bg_p_face(p, k));
                         }
                         cons_to_prim(nd, p->gamma, 0.0, u, wc[s]);
                         if (!(wc[s][0] > 0.0) || !(wc[s][nd + 1] > 0.0)) bad = 1;
+                        wc[s][0] -= rb;
+                        wc[s][nd + 1] -= pb;
                     }
                     if (bad) continue;
                     for (int s = 0; s < 2; ++s)
@@ -646,7 +665,17 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
                         for (int e = 0; e < nd; ++e) r[1 + e] = -un * dw[d][1 + e] / g->dx[d];
                         r[1 + d] -= dw[d][nd + 1] / rho / g->dx[d];
                         r[nd + 1] = -(un * dw[d][nd + 1] + gam * pr * dw[d][1 + d]) / g->dx[d];
-                        for (int e = 0; e < nd; ++e) r[1 + e] += p->grav[e] * (w[0] / rho);
+                        if (p->hse && d == 2) {   /* advection of the background along z */
+                            r[0] -= w[3] * drho_bg / g->dx[2];
+                            r[4] -= w[3] * dp_bg / g->dx[2];
+                        }
+                        /* gravity on the velocities in every axis's predictor: g,
+                           except in the z predictor of hse mode, which takes the
+                           background's pressure gradient from its imbalance
+                           instead (g rho'/rho - B/rho) */
+                        const double gf = (p->hse && d == 2) ? w[0] / rho : 1.0;
+                        for (int e = 0; e < nd; ++e) r[1 + e] += p->grav[e] * gf;
+                        if (p->hse && d == 2) r[3] -= B / rho;
                         for (int q = 0; q < nv; ++q) wd[d][q] = w[q] + hdt * r[q];
                     }
 
@@ -687,6 +716,10 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
                     for (int d = 0; d < nd; ++d)
                         for (int s = 0; s < 2; ++s)
                             for (int q = 0; q < nv; ++q) wf[d][s][q] = w0[q];
+                    if (mode == MODE_CTU && p->hse)   /* x and y states: plain gravity (as their predictor) */
+                        for (int d = 0; d < nd && d < 2; ++d)
+                            for (int s = 0; s < 2; ++s)
+                                for (int e = 0; e < nd; ++e) wf[d][s][1 + e] = w[1 + e] + hdt * p->grav[e];
                 }
                 for (int d = 0; d < nd; ++d)
                     for (int s = 0; s < 2; ++s)

@@ -22,7 +22,8 @@ from paper_1510_05061_gb300 import inputs
 from paper_1510_05061_gb300.inputs import BC_OUTFLOW, BC_PERIODIC, BC_REFLECT, CTU, Problem
 
 from test_oracle_rk2 import mc_slopes
-from test_oracle_scheme import SOD_L, SOD_R, l1rel, potential_totals, restrict2, smooth_random_prim
+from test_oracle_scheme import (SOD_L, SOD_R, l1rel, potential_totals, restrict2, smooth_random_prim,
+                                with_background)
 
 THREADS = 8
 
@@ -245,10 +246,107 @@ def test_ctu_reflecting_walls_mass_and_energy_with_potential(orc):
     assert abs(e1 - e0) <= 1e-12 * abs(e0), (e1 - e0)
 
 
+# ------------------------------------------------ hydrostatic background
+def test_ctu_hse_constant_background_with_gravity_equals_plain(orc):
+    """A constant background out of balance: its imbalance B_k = -rho0 g
+    must reproduce the full gravity force in the predictors, the transverse
+    corrections and the update."""
+    prob = ctu(Problem(ndim=3, n=(9, 8, 12), hi=(1.0, 1.0, 2.0),
+                       bc_lo=(BC_PERIODIC, BC_OUTFLOW, BC_REFLECT),
+                       bc_hi=(BC_PERIODIC, BC_REFLECT, BC_REFLECT), grav=(0.0, 0.0, -0.9)))
+    W = smooth_random_prim(prob, 8)
+    nz = prob.n[2]
+    hp = with_background(prob, np.full(nz + 4, 0.8), np.full(nz + 4, 0.6),
+                         np.full(nz + 5, 0.8), np.full(nz + 5, 0.6))
+    o, U, V, t, s = run(orc, prob, W, max_steps=30)
+    oh, Uh, Vh, th, sh = run(orc, hp, W, max_steps=30)
+    T, Th = o.total(V), oh.total(Vh)
+    for q in range(prob.nvar):
+        assert l1rel(Th[q], T[q]) <= 1e-12
+
+
+def test_ctu_hse_balanced_background_stays_at_rest(orc):
+    prob, _ = inputs.rayleigh_taylor(8, nz=16, perturb=False)
+    prob = ctu(prob)
+    nz, dz, g = prob.n[2], prob.dx()[2], -1.0
+    zc = (np.arange(-2, nz + 2) + 0.5) * dz
+    zf = np.arange(-2, nz + 3) * dz
+    hp = with_background(prob, np.ones(nz + 4), 3.0 + g * zc, np.ones(nz + 5), 3.0 + g * zf)
+    W = np.zeros(prob.shape)
+    W[0] = 1.0
+    W[4] = (3.0 + g * prob.centres(2))[:, None, None]
+    oh, Uh, Vh, _, _ = run(orc, hp, W, max_steps=40)
+    assert np.abs(Vh[1:4]).max() <= 1e-13
+    o, U, V, _, _ = run(orc, prob, W, max_steps=40)
+    assert np.abs(V[3]).max() > 1e-6
+
+
+def test_ctu_hse_one_step_equals_plain_on_linear_data(orc):
+    nz = 16
+    prob = ctu(Problem(ndim=3, n=(5, 4, nz), hi=(1.0, 1.0, 2.0),
+                       bc_lo=(BC_PERIODIC, BC_PERIODIC, BC_REFLECT),
+                       bc_hi=(BC_PERIODIC, BC_PERIODIC, BC_REFLECT), grav=(0.0, 0.0, -0.7)))
+    dz = prob.dx()[2]
+    zc = (np.arange(-2, nz + 2) + 0.5) * dz
+    zf = np.arange(-2, nz + 3) * dz
+    hp = with_background(prob, 1.0 + 0.3 * zc, 2.0 - 0.5 * zc, 1.0 + 0.3 * zf, 2.0 - 0.5 * zf)
+    z = prob.centres(2)
+    W = np.zeros(prob.shape)
+    W[0] = (1.2 + 0.1 * z)[:, None, None]
+    W[1], W[2], W[3] = 0.1, -0.2, 0.15
+    W[4] = (2.1 - 0.4 * z)[:, None, None]
+    o, oh = orc.Oracle(prob), orc.Oracle(hp)
+    U, Uh = o.state_from_prim(W), oh.state_from_prim(W)
+    dt = 0.5 * o.cfl_dt(U)
+    T = o.total(o.step(U, dt))
+    Th = oh.total(oh.step(Uh, dt))
+    inner = slice(3, nz - 3)
+    for q in range(prob.nvar):
+        a, b = Th[q, inner], T[q, inner]
+        assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(b).max()), q
+    assert np.abs(Th[4] - T[4]).max() > 1e-10
+
+
+def test_ctu_hse_one_step_equals_plain_with_shear(orc):
+    """Density and pressure linear in z, velocities varying across x and y:
+    the transverse corrections of z-face states then change velocities, and
+    their conversions see the background at the face."""
+    nz = 16
+    prob = ctu(Problem(ndim=3, n=(12, 10, nz), hi=(1.0, 1.0, 2.0),
+                       bc_lo=(BC_PERIODIC, BC_PERIODIC, BC_REFLECT),
+                       bc_hi=(BC_PERIODIC, BC_PERIODIC, BC_REFLECT), grav=(0.0, 0.0, -0.7)))
+    dz = prob.dx()[2]
+    zc = (np.arange(-2, nz + 2) + 0.5) * dz
+    zf = np.arange(-2, nz + 3) * dz
+    hp = with_background(prob, 1.0 + 0.3 * zc, 2.0 - 0.5 * zc, 1.0 + 0.3 * zf, 2.0 - 0.5 * zf)
+    x, y, z = prob.centres(0), prob.centres(1), prob.centres(2)
+    W = np.zeros(prob.shape)
+    W[0] = (1.2 + 0.1 * z)[:, None, None]
+    W[1] = (0.1 + 0.2 * np.sin(2 * np.pi * y))[None, :, None]
+    W[2] = (-0.2 + 0.2 * np.cos(2 * np.pi * x))[None, None, :]
+    W[3] = 0.15 + 0.1 * np.sin(2 * np.pi * x)[None, None, :] * np.cos(2 * np.pi * y)[None, :, None]
+    W[4] = (2.1 - 0.4 * z)[:, None, None]
+    o, oh = orc.Oracle(prob), orc.Oracle(hp)
+    U, Uh = o.state_from_prim(W), oh.state_from_prim(W)
+    dt = 0.5 * o.cfl_dt(U)
+    T = o.total(o.step(U, dt))
+    Th = oh.total(oh.step(Uh, dt))
+    inner = slice(3, nz - 3)
+    for q in range(prob.nvar):
+        a, b = Th[q, inner], T[q, inner]
+        assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(b).max()), q
+
+
+def test_ctu_hse_reflecting_walls_mass_and_energy_with_potential(orc):
+    prob, W = inputs.rayleigh_taylor(12, nz=24, amplitude=0.05, hse_subtract=1)
+    o, U, V, t, s = run(orc, ctu(prob), W, max_steps=60)
+    m0, e0 = potential_totals(o, prob, U)
+    m1, e1 = potential_totals(o, prob, V)
+    assert abs(m1 - m0) <= 1e-13 * m0
+    assert abs(e1 - e0) <= 1e-12 * abs(e0), (e1 - e0)
+
+
 def test_ctu_rejected_combinations(orc):
-    prt, Wrt = inputs.rayleigh_taylor(8, nz=8, hse_subtract=1)
-    with pytest.raises(ValueError):
-        orc.Oracle(ctu(prt)).state_from_prim(Wrt)
     ps, Ws = inputs.sod(16)
     with pytest.raises(ValueError):
         orc.Oracle(ctu(ps).replace(recon=inputs.PPM)).state_from_prim(Ws)
