@@ -100,8 +100,9 @@ CONFIGS = {
                            desc="3D Rayleigh-Taylor 512^3 FP32 (FP64 dt and reductions), SSP-RK2 with PPM"),
     "rt256-fp64-ctu": dict(n=256, precision=inputs.FP64, hse=0, scheme=inputs.CTU,
                            desc="3D Rayleigh-Taylor 256^3 FP64, corner transport upwind (one fused kernel per step)"),
-    "rt512-fp32-ctu": dict(n=512, precision=inputs.FP32, hse=0, scheme=inputs.CTU,
-                           desc="3D Rayleigh-Taylor 512^3 FP32 (FP64 dt and reductions), corner transport upwind"),
+    "rt512-fp32-ctu": dict(n=512, precision=inputs.FP32, hse=1, scheme=inputs.CTU,
+                           desc="3D Rayleigh-Taylor 512^3 FP32 bulk with background subtraction, corner "
+                                "transport upwind"),
     "rt256-fp64-slabs4": dict(n=256, precision=inputs.FP64, hse=0, slabs=4,
                               desc="3D Rayleigh-Taylor 256^3 FP64 cut into 4 z slabs run as virtual ranks "
                                    "(depth-2 halo exchange + dt max-reduction every step)"),
@@ -307,9 +308,25 @@ def build_workload(cfg):
 
 
 # --------------------------------------------------------------- oracle
-def oracle_sample(seconds: float = 10.0, max_steps: int = 1000, cfg="rt256-fp64", nz_slab=None):
+def host_cpu_model() -> str:
+    """The host CPU's model name as lscpu prints it ("" when unavailable)."""
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for line in out.splitlines():
+        if line.strip().startswith("Model name:"):
+            return line.split(":", 1)[1].strip()
+    return ""
+
+
+def oracle_sample(seconds: float = 10.0, max_steps: int = 1000, cfg="rt256-fp64", nz_slab=None,
+                  threads: int = 0):
     """Time the FP64 CPU oracle, as it stands, on a bounded sample of the
-    workload.  Returns (zone-updates/s, cores, sample description)."""
+    workload, on all host cores (threads = 0) or on the given number of
+    threads.  Returns (zone-updates/s, cores, sample description)."""
     import oracle
 
     oracle.build()
@@ -327,7 +344,7 @@ def oracle_sample(seconds: float = 10.0, max_steps: int = 1000, cfg="rt256-fp64"
         prob = prob.replace(**kw)
         W = np.ascontiguousarray(W[:, k0:k0 + nz_slab])
         desc = f"{prob.n[0]}x{prob.n[1]}x{nz_slab} slab of the {c['n']}^3 initial state around the interface"
-    o = oracle.Oracle(prob)
+    o = oracle.Oracle(prob, threads=threads)
     U = o.state_from_prim(W)
     cores = o.L.orc_max_threads()
     done, t0 = 0, time.perf_counter()
@@ -703,7 +720,7 @@ def run_gpu(args):
     knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}>"
                if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
     if prob.scheme == inputs.CTU:
-        knames = [f"ctu3d_kernel<{tname}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3
+        knames = [f"ctu3d_kernel<{tname}, {prob.hse_subtract}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3
                   else f"ctu2d_kernel<{tname}, 32, 8>"]
     kname = " + ".join(knames)
     # DRAM bytes of one step: the sum over its kernels (null if any is missing or stale)
@@ -730,7 +747,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = oracle_sample(cfg=args.config, nz_slab=32)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v1, _, sample1 = oracle_sample(seconds=5.0, cfg=args.config, nz_slab=8, threads=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "cpu_model": host_cpu_model(),
+               "one_core": {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}}
 
     if rank == 0:
         line = {

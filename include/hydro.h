@@ -75,7 +75,12 @@ enum { HYDRO_SCHEME_HANCOCK = 0, HYDRO_SCHEME_SSPRK2 = 1, HYDRO_SCHEME_CTU = 2 }
 /* CTU: the unsplit corner transport upwind method (Colella 1990): per axis a
    one-dimensional MUSCL-Hancock predictor, first-pass HLLC fluxes, face
    states corrected by the transverse flux differences, final HLLC fluxes;
-   one kernel per step.  PLM and hse_subtract = 0 only. */
+   one kernel per step; PLM only.  With hse_subtract = 1 the step is written
+   on the perturbations: the z predictor advects the background and takes
+   g rho'/rho - B_k/rho, the x and y predictors take g, face states are
+   corrected as total states, and the x and y states' z-momentum correction
+   adds the background's pressure difference across the cell (the first-pass
+   z fluxes carry p'). */
 /* Face-state reconstruction.  PLM: MC-limited piecewise linear (van Leer
    1977).  PPM: the piecewise parabolic method (Colella and Woodward 1984):
    interface values from the MC-limited slopes, parabola limited to be

@@ -23,10 +23,10 @@ int ctu_zchunk(const int n[3], bool fp32)
     return (int)((n[2] + nch - 1) / nch);
 }
 
-template <typename T, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY>
 cudaError_t launch_ctu(const StepArgs &a0, cudaStream_t s)
 {
-    auto k = ctu3d_kernel<T, TX, TY>;
+    auto k = ctu3d_kernel<T, HSE, TX, TY>;
     constexpr size_t smem = Ctu3DSmem<T, TX, TY>::bytes;
     static bool configured = false;
     if (!configured) {
@@ -50,9 +50,10 @@ long long ctu3d_blocks(const int n[3], bool fp32)
     return (long long)((n[0] + CTU_TX - 1) / CTU_TX) * ((n[1] + ctu_ty(fp32) - 1) / ctu_ty(fp32)) * n[2];
 }
 
-cudaError_t launch_ctu3d(const StepArgs &a, cudaStream_t s, bool fp32)
+cudaError_t launch_ctu3d(const StepArgs &a, cudaStream_t s, bool fp32, bool hse)
 {
-    return fp32 ? launch_ctu<float, 16, 16>(a, s) : launch_ctu<double, 16, 8>(a, s);
+    if (hse) return fp32 ? launch_ctu<float, true, 16, 16>(a, s) : launch_ctu<double, true, 16, 8>(a, s);
+    return fp32 ? launch_ctu<float, false, 16, 16>(a, s) : launch_ctu<double, false, 16, 8>(a, s);
 }
 
 }  // namespace hydro

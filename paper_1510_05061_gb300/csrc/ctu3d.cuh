@@ -22,6 +22,17 @@
 //      the z face p-1/2 from the corrected states and completes plane p-1:
 //      MUSCL-Hancock update and sources, store, CFL signal speed.
 // Reflecting walls mirror the near-side state on both passes.
+//
+// In the hydrostatic-background mode (HSE) the step is the plain one written
+// on the perturbations rho', p' of the stored state: the z predictor advects
+// the background and takes g rho'/rho - B_k/rho for gravity, the x and y
+// predictors take g; the correction acts on the total state of each face
+// (the background's density and pressure at that face added), which is the
+// same as correcting the perturbation's density and energy with the total
+// density in the momentum and kinetic energy; since the first-pass z fluxes
+// carry p', the x and y states' z-momentum correction adds the background's
+// pressure difference across the cell; HLLC sees total states and its
+// normal momentum flux carries p'; the update takes -B_k on the z momentum.
 #pragma once
 
 #include <type_traits>
@@ -48,7 +59,70 @@ struct Ctu3DSmem {
     static_assert(bytes <= 226 * 1024, "shared memory of one CTA");
 };
 
-template <typename T, int TX, int TY>
+// Conserved variables of a face state: density and energy of the
+// perturbation, momentum of the total state (HSE: total density rb + w[0]);
+// without background the plain conversion.
+template <typename T, bool HSE>
+__device__ __forceinline__ void prim_to_cons_bg(const T (&w)[5], T rb, T igm1, T (&u)[5])
+{
+    const T rho = HSE ? rb + w[0] : w[0];
+    T ke = T(0);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        u[1 + e] = rho * w[1 + e];
+        ke += w[1 + e] * w[1 + e];
+    }
+    u[0] = w[0];
+    u[4] = w[4] * igm1 + T(0.5) * rho * ke;
+}
+
+template <typename T, bool HSE>
+__device__ __forceinline__ void cons_to_prim_bg(const T (&u)[5], T rb, T gam, T (&w)[5])
+{
+    const T rinv = rcp_t(HSE ? rb + u[0] : u[0]);
+    T m2 = T(0);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        w[1 + e] = u[1 + e] * rinv;
+        m2 += u[1 + e] * u[1 + e];
+    }
+    w[0] = u[0];
+    w[4] = (gam - T(1)) * (u[4] - T(0.5) * m2 * rinv);
+}
+
+// One-dimensional MUSCL-Hancock predictor along axis d of a cell in the
+// hydrostatic-background mode: the perturbation's A_d terms with the total
+// density and pressure; along z the background's advection and
+// g rho'/rho - B/rho, along x and y plain gravity.
+template <typename T>
+__device__ __forceinline__ void predict_axis_bg(const T (&w)[5], const T (&dwd)[5], int d, T hdt, T inv_dxd,
+                                                T gam, const T (&grav)[3], const CellBG<T> &bg, T (&wd)[5])
+{
+    const T rho = bg.rho + w[0], pr = bg.p + w[4];
+    const T un = w[1 + d];
+    const T rinv = rcp_t(rho);
+    T r[5];
+    r[0] = -(un * dwd[0] + rho * dwd[1 + d]) * inv_dxd;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) r[1 + e] = -un * dwd[1 + e] * inv_dxd;
+    r[1 + d] -= dwd[4] * rinv * inv_dxd;
+    r[4] = -(un * dwd[4] + gam * pr * dwd[1 + d]) * inv_dxd;
+    if (d == 2) {
+        r[0] -= w[3] * bg.drho * inv_dxd;
+        r[4] -= w[3] * bg.dp * inv_dxd;
+        const T rr = w[0] * rinv;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) r[1 + e] += grav[e] * rr;
+        r[3] -= bg.B * rinv;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) r[1 + e] += grav[e];
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) wd[q] = w[q] + hdt * r[q];
+}
+
+template <typename T, bool HSE, int TX, int TY>
 __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chunk, double dtd,
                                            unsigned char *smem_raw, T &smax, bool &bad)
 {
@@ -69,6 +143,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
     const int z1 = min(z0 + a.zchunk, nz);
     const T *__restrict__ U = static_cast<const T *>(a.U);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
+    const PlaneBGT<T> *bgT = static_cast<const PlaneBGT<T> *>(a.bgT);
     const long long vs = a.vstride;
     const int plane = static_cast<int>(a.plane);
     const int gx = x0 + tx, gy = y0 + ty;
@@ -101,6 +176,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
         bool fz;
         const int sz = map_index(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
         const T *Up = U + (long long)sz * plane;
+        const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
         for (int i = tid; i < HX * HY; i += NT) {
             const int hx = i % HX, hy = i / HX;
             bool fx, fy;
@@ -113,7 +189,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             if (fx) m0 = -m0;
             if (fy) m1 = -m1;
             if (fz) m2 = -m2;
-            const T rinv = rcp_t(r);
+            const T rinv = rcp_t(HSE ? rho_bg + r : r);
             P(slot, 0, hy, hx) = r;
             P(slot, 1, hy, hx) = m0 * rinv;
             P(slot, 2, hy, hx) = m1 * rinv;
@@ -126,6 +202,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
     auto predict_plane = [&](int p) {
         const int b = p & 1;
         const int s0 = (p + 6) % 3, sm = (p + 5) % 3, sp = (p + 7) % 3;
+        const CellBG<T> bg = cell_bg<T, HSE>(bgT, p);
         for (int i = tid; i < EX * EY; i += NT) {
             const int cx = i % EX - 1, cy = i / EX - 1;
             const int hx = cx + 2, hy = cy + 2;
@@ -142,18 +219,43 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             bool ok = true;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                predict_axis<T, ND>(w, dw[d], d, hdt, inv_dx[d], gam, grav, wd[d]);
-                ok = ok && positive(wd[d][0] - T(0.5) * dw[d][0]) && positive(wd[d][0] + T(0.5) * dw[d][0])
-                        && positive(wd[d][NV - 1] - T(0.5) * dw[d][NV - 1])
-                        && positive(wd[d][NV - 1] + T(0.5) * dw[d][NV - 1]);
+                if constexpr (HSE) {
+                    predict_axis_bg<T>(w, dw[d], d, hdt, inv_dx[d], gam, grav, bg, wd[d]);
+                    // total face density and pressure: the plane's centre
+                    // background for x and y, the z faces' own along z
+                    const T rlo = d == 2 ? bg.rho_lo : bg.rho, rhi = d == 2 ? bg.rho_hi : bg.rho;
+                    const T plo = d == 2 ? bg.p_lo : bg.p, phi = d == 2 ? bg.p_hi : bg.p;
+                    ok = ok && positive(rlo + (wd[d][0] - T(0.5) * dw[d][0]))
+                            && positive(rhi + (wd[d][0] + T(0.5) * dw[d][0]))
+                            && positive(plo + (wd[d][NV - 1] - T(0.5) * dw[d][NV - 1]))
+                            && positive(phi + (wd[d][NV - 1] + T(0.5) * dw[d][NV - 1]));
+                } else {
+                    predict_axis<T, ND>(w, dw[d], d, hdt, inv_dx[d], gam, grav, wd[d]);
+                    ok = ok && positive(wd[d][0] - T(0.5) * dw[d][0]) && positive(wd[d][0] + T(0.5) * dw[d][0])
+                            && positive(wd[d][NV - 1] - T(0.5) * dw[d][NV - 1])
+                            && positive(wd[d][NV - 1] + T(0.5) * dw[d][NV - 1]);
+                }
             }
             if (!ok) {
+                // zero slopes: every face takes the cell state plus half a
+                // step of gravity (HSE: the z states the MUSCL-Hancock
+                // source g rho'/rho - B/rho, the x and y states g)
+                T gz[ND];
+#pragma unroll
+                for (int e = 0; e < ND; ++e) gz[e] = grav[e];
+                if constexpr (HSE) {
+                    const T rinv = rcp_t(bg.rho + w[0]);
+#pragma unroll
+                    for (int e = 0; e < ND; ++e) gz[e] = grav[e] * (w[0] * rinv);
+                    gz[2] -= bg.B * rinv;
+                }
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
 #pragma unroll
                     for (int q = 0; q < NV; ++q) {
                         dw[d][q] = T(0);
-                        wd[d][q] = w[q] + (q >= 1 && q <= ND ? hdt * grav[q - 1] : T(0));
+                        const T gq = q >= 1 && q <= ND ? (d == 2 ? gz[q - 1] : grav[q - 1]) : T(0);
+                        wd[d][q] = w[q] + (q >= 1 && q <= ND ? hdt * gq : T(0));
                     }
             }
 #pragma unroll
@@ -168,7 +270,8 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
 
     // HLLC from a left and a right state array along axis D; a wall at the
     // face mirrors the near side
-    auto hllc_mirror = [&](auto DC, bool w_lo, bool w_hi, const T (&vl)[NV], const T (&vr)[NV], T (&f)[NV]) {
+    auto hllc_mirror = [&](auto DC, bool w_lo, bool w_hi, const T (&vl)[NV], const T (&vr)[NV], T rb, T pb,
+                           T (&f)[NV]) {
         constexpr int D = decltype(DC)::value;
         T wl[NV], wr[NV];
 #pragma unroll
@@ -176,12 +279,13 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             wl[q] = w_lo ? (q == 1 + D ? -vr[q] : vr[q]) : vl[q];
             wr[q] = w_hi ? (q == 1 + D ? -vl[q] : vl[q]) : vr[q];
         }
-        hllc<T, ND, D, false>(wl, wr, T(0), T(0), gam, igm1, f);
+        hllc<T, ND, D, HSE>(wl, wr, rb, pb, gam, igm1, f);
     };
     using D0 = std::integral_constant<int, 0>;
     using D1 = std::integral_constant<int, 1>;
     using D2 = std::integral_constant<int, 2>;
-    auto x_face = [&](int b, int cy, int fi, T (&f)[NV]) {
+    // x and y faces of plane pl (parity b): the plane's centre background
+    auto x_face = [&](int b, int pl, int cy, int fi, T (&f)[NV]) {
         const int gf = x0 + fi;
         T vl[NV], vr[NV];
 #pragma unroll
@@ -189,9 +293,10 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             vl[q] = SE(b, 1, q, cy, fi - 1);
             vr[q] = SE(b, 0, q, cy, fi);
         }
-        hllc_mirror(D0{}, gf == 0 && a.bc_lo[0] == BC_REFLECT, gf == nx && a.bc_hi[0] == BC_REFLECT, vl, vr, f);
+        hllc_mirror(D0{}, gf == 0 && a.bc_lo[0] == BC_REFLECT, gf == nx && a.bc_hi[0] == BC_REFLECT, vl, vr,
+                    HSE ? bgT[pl + 2].rho_c : T(0), HSE ? bgT[pl + 2].p_c : T(0), f);
     };
-    auto y_face = [&](int b, int fj, int cx, T (&f)[NV]) {
+    auto y_face = [&](int b, int pl, int fj, int cx, T (&f)[NV]) {
         const int gf = y0 + fj;
         T vl[NV], vr[NV];
 #pragma unroll
@@ -199,10 +304,12 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             vl[q] = SE(b, 3, q, fj - 1, cx);
             vr[q] = SE(b, 2, q, fj, cx);
         }
-        hllc_mirror(D1{}, gf == 0 && a.bc_lo[1] == BC_REFLECT, gf == ny && a.bc_hi[1] == BC_REFLECT, vl, vr, f);
+        hllc_mirror(D1{}, gf == 0 && a.bc_lo[1] == BC_REFLECT, gf == ny && a.bc_hi[1] == BC_REFLECT, vl, vr,
+                    HSE ? bgT[pl + 2].rho_c : T(0), HSE ? bgT[pl + 2].p_c : T(0), f);
     };
     // z face below plane p between the high state of plane p-1 (array hi: 5
-    // first pass, 6 corrected) and the low state of plane p
+    // first pass, 6 corrected) and the low state of plane p; the face's own
+    // background
     auto z_face = [&](int p, int hi, int cy, int cx, T (&f)[NV]) {
         T vl[NV], vr[NV];
 #pragma unroll
@@ -210,14 +317,16 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             vl[q] = SE((p - 1) & 1, hi, q, cy, cx);
             vr[q] = SE(p & 1, 4, q, cy, cx);
         }
-        hllc_mirror(D2{}, p == 0 && a.bc_lo[2] == BC_REFLECT, p == nz && a.bc_hi[2] == BC_REFLECT, vl, vr, f);
+        hllc_mirror(D2{}, p == 0 && a.bc_lo[2] == BC_REFLECT, p == nz && a.bc_hi[2] == BC_REFLECT, vl, vr,
+                    HSE ? bgT[p + 2].rho_f : T(0), HSE ? bgT[p + 2].p_f : T(0), f);
     };
 
     // transverse correction of both face states of a cell (arrays lo, lo + 1)
     // into arrays dlo, dhi (the uncorrected pair when a corrected density or
-    // pressure would not be positive)
+    // pressure would not be positive).  rb, pb: the background at the two
+    // faces; dmz: the extra z-momentum correction of HSE x and y states.
     auto correct = [&](int b, int lo, int dlo, int dhi, int cy, int cx, const T (&d1)[NV], T k1,
-                       const T (&d2)[NV], T k2) {
+                       const T (&d2)[NV], T k2, const T (&rb)[2], const T (&pb)[2], T dmz) {
         T wc[2][NV];
         bool ok = true;
 #pragma unroll
@@ -225,13 +334,15 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             T w[NV], u[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) w[q] = SE(b, lo + s, q, cy, cx);
-            prim_to_cons_t<T, ND>(w, igm1, u);
+            prim_to_cons_bg<T, HSE>(w, rb[s], igm1, u);
 #pragma unroll
             for (int q = 0; q < NV; ++q) u[q] -= k1 * d1[q];
 #pragma unroll
             for (int q = 0; q < NV; ++q) u[q] -= k2 * d2[q];
-            cons_to_prim_t<T, ND>(u, gam, wc[s]);
-            ok = ok && positive(wc[s][0]) && positive(wc[s][NV - 1]);
+            if constexpr (HSE) u[3] -= dmz;
+            cons_to_prim_bg<T, HSE>(u, rb[s], gam, wc[s]);
+            ok = ok && positive(HSE ? rb[s] + wc[s][0] : wc[s][0])
+                    && positive(HSE ? pb[s] + wc[s][NV - 1] : wc[s][NV - 1]);
         }
         if (ok) {
 #pragma unroll
@@ -264,14 +375,14 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
         for (int i = tid; i < (TX + 1) * EY; i += NT) {
             const int fi = i % (TX + 1), cy = i / (TX + 1) - 1;
             T f[NV];
-            x_face(b, cy, fi, f);
+            x_face(b, p, cy, fi, f);
 #pragma unroll
             for (int q = 0; q < NV; ++q) FX(b, q, cy, fi) = f[q];
         }
         for (int i = tid; i < EX * (TY + 1); i += NT) {
             const int cx = i % EX - 1, fj = i / EX;
             T f[NV];
-            y_face(b, fj, cx, f);
+            y_face(b, p, fj, cx, f);
 #pragma unroll
             for (int q = 0; q < NV; ++q) FY(b, q, fj, cx) = f[q];
         }
@@ -288,6 +399,15 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
 
         // 4. corrections: z states of plane p (tile cells), x and y states of
         // plane p-1 (its z faces' first-pass fluxes are now both known)
+        T rbz[2] = {T(0), T(0)}, pbz[2] = {T(0), T(0)}, rbc[2] = {T(0), T(0)}, pbc[2] = {T(0), T(0)};
+        T dmz = T(0);
+        if constexpr (HSE) {
+            rbz[0] = bgT[p + 2].rho_f; rbz[1] = bgT[p + 3].rho_f;
+            pbz[0] = bgT[p + 2].p_f;   pbz[1] = bgT[p + 3].p_f;
+            rbc[0] = rbc[1] = bgT[p + 1].rho_c;
+            pbc[0] = pbc[1] = bgT[p + 1].p_c;
+            dmz = hdt_dx[2] * bgT[p + 1].dp;
+        }
         for (int i = tid; i < TX * TY; i += NT) {
             const int cx = i % TX, cy = i / TX;
             T dx1[NV], dy1[NV];
@@ -296,7 +416,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
                 dx1[q] = FX(b, q, cy, cx + 1) - FX(b, q, cy, cx);
                 dy1[q] = FY(b, q, cy + 1, cx) - FY(b, q, cy, cx);
             }
-            correct(b, 4, 4, 6, cy, cx, dx1, hdt_dx[0], dy1, hdt_dx[1]);
+            correct(b, 4, 4, 6, cy, cx, dx1, hdt_dx[0], dy1, hdt_dx[1], rbz, pbz, T(0));
         }
         const bool out_plane = p - 1 >= z0 && p - 1 < z1;   // plane p-1 is completed now
         if (out_plane) {
@@ -308,7 +428,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
                     dy1[q] = FY(bm, q, cy + 1, cx) - FY(bm, q, cy, cx);
                     dz1[q] = FZ(b, q, cy, cx) - FZ(bm, q, cy, cx);
                 }
-                correct(bm, 0, 0, 1, cy, cx, dy1, hdt_dx[1], dz1, hdt_dx[2]);
+                correct(bm, 0, 0, 1, cy, cx, dy1, hdt_dx[1], dz1, hdt_dx[2], rbc, pbc, dmz);
             }
             for (int i = tid; i < TX * EY; i += NT) {        // y states: tile columns, rows -1..TY
                 const int cx = i % TX, cy = i / TX - 1;
@@ -318,7 +438,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
                     dx1[q] = FX(bm, q, cy, cx + 1) - FX(bm, q, cy, cx);
                     dz1[q] = FZ(b, q, cy, cx) - FZ(bm, q, cy, cx);
                 }
-                correct(bm, 2, 2, 3, cy, cx, dx1, hdt_dx[0], dz1, hdt_dx[2]);
+                correct(bm, 2, 2, 3, cy, cx, dx1, hdt_dx[0], dz1, hdt_dx[2], rbc, pbc, dmz);
             }
         }
         __syncthreads();
@@ -329,14 +449,14 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             for (int i = tid; i < (TX + 1) * TY; i += NT) {
                 const int fi = i % (TX + 1), cy = i / (TX + 1);
                 T f[NV];
-                x_face(bm, cy, fi, f);
+                x_face(bm, p - 1, cy, fi, f);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) FX(bm, q, cy, fi) = f[q];
             }
             for (int i = tid; i < TX * (TY + 1); i += NT) {
                 const int cx = i % TX, fj = i / TX;
                 T f[NV];
-                y_face(bm, fj, cx, f);
+                y_face(bm, p - 1, fj, cx, f);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) FY(bm, q, fj, cx) = f[q];
             }
@@ -345,7 +465,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
         if (p >= z0) z_face(p, 6, ty, tx, fz);
         __syncthreads();
 
-        // update of plane p-1 (MUSCL-Hancock sources)
+        // update of plane p-1 (MUSCL-Hancock sources; HSE: -B on the z momentum)
         if (out_plane && own) {
             const long long c = (long long)(p - 1) * plane + own_off;
             T u[NV], du[NV];
@@ -364,17 +484,23 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             u[0] = r_new;
             const T rsum = T(0.5) * (r_old + r_new);
 #pragma unroll
-            for (int d = 0; d < ND; ++d) u[1 + d] += dt * (du[1 + d] + grav[d] * rsum);
+            for (int d = 0; d < ND; ++d) {
+                T src = grav[d] * rsum;
+                if (HSE && d == 2) src -= bgT[p + 1].B;
+                u[1 + d] += dt * (du[1 + d] + src);
+            }
             u[4] += dt * (du[4] + msrc);
 #pragma unroll
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
-            const T rinv = rcp_t(u[0]);
+            const T rho = HSE ? bgT[p + 1].rho_c + u[0] : u[0];
+            const T rinv = rcp_t(rho);
             const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
-            const T pres = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
+            const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
+            const T pres = HSE ? bgT[p + 1].p_c + pp : pp;
             const T gp = gam * pres;
-            const T cs = gp * rsqrt_t(gp * u[0]);
+            const T cs = gp * rsqrt_t(gp * rho);
             const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
-            if (!(u[0] > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
+            if (!(rho > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
             else smax = fmax(smax, s);
         }
         if (p >= z0) {
@@ -384,7 +510,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
     }
 }
 
-template <typename T, int TX, int TY>
+template <typename T, bool HSE, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) ctu3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
@@ -412,7 +538,7 @@ __global__ void __launch_bounds__(TX * TY) ctu3d_kernel(const StepArgs a)
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    ctu3d_body<T, TX, TY>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    ctu3d_body<T, HSE, TX, TY>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     const double m = block_max_t<NT, T>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd, true,

@@ -76,7 +76,7 @@ int check_problem(const hydro_problem *p)
     if (p->hse_subtract != 0 && p->hse_subtract != 1) return HYDRO_ERR_INVALID_ARG;
     if (p->scheme != HYDRO_SCHEME_HANCOCK && p->scheme != HYDRO_SCHEME_SSPRK2 && p->scheme != HYDRO_SCHEME_CTU)
         return HYDRO_ERR_INVALID_ARG;
-    if (p->scheme == HYDRO_SCHEME_CTU && (p->hse_subtract || p->recon != HYDRO_RECON_PLM))
+    if (p->scheme == HYDRO_SCHEME_CTU && p->recon != HYDRO_RECON_PLM)
         return HYDRO_ERR_INVALID_ARG;
     if (p->recon != HYDRO_RECON_PLM && p->recon != HYDRO_RECON_PPM) return HYDRO_ERR_INVALID_ARG;
     if (p->recon == HYDRO_RECON_PPM) {
@@ -250,7 +250,7 @@ cudaError_t launch_kernel(hydro_sim *s, const StepArgs &a, int stage)
         return launch_ctu2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32);
     if (s->prob.ndim == 2)
         return launch_step2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32, stage, recon);
-    if (s->prob.scheme == HYDRO_SCHEME_CTU) return launch_ctu3d(a, s->stream, fp32);
+    if (s->prob.scheme == HYDRO_SCHEME_CTU) return launch_ctu3d(a, s->stream, fp32, hse);
     const dim3 grid(s->tiles_x * s->tiles_y, (s->prob.n[2] + s->zchunk - 1) / s->zchunk);
     if (stage == STAGE_HANCOCK)
         return fp32 ? launch_step3d_f32(s->variant, a, grid, s->stream, hse)

@@ -65,7 +65,7 @@ cudaError_t launch_step2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp3
 // corner transport upwind step (2D: same tile as the 2D step; 3D: blocks of
 // cells, ctu3d_blocks of them)
 cudaError_t launch_ctu2d(const StepArgs &a, dim3 grid, cudaStream_t s, bool fp32);
-cudaError_t launch_ctu3d(const StepArgs &a, cudaStream_t s, bool fp32);
+cudaError_t launch_ctu3d(const StepArgs &a, cudaStream_t s, bool fp32, bool hse);
 long long ctu3d_blocks(const int n[3], bool fp32);
 
 // Auxiliary kernels (aux.cu).  fp32 selects the stored precision.

@@ -43,7 +43,7 @@ FP32 = 1
 
 HANCOCK = 0   # single-stage unsplit MUSCL-Hancock
 SSPRK2 = 1    # two-stage SSP Runge-Kutta method of lines
-CTU = 2       # corner transport upwind (Colella 1990), PLM, no background
+CTU = 2       # corner transport upwind (Colella 1990), PLM
 
 PLM = 0       # piecewise linear reconstruction, MC limiter
 PPM = 1       # piecewise parabolic reconstruction (SSPRK2, no hse)
