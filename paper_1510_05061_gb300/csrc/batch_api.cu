@@ -226,6 +226,7 @@ int rebuild(hydro_batch *b)
                                                    : static_cast<const void *>(I.bg);
             a.zchunk = zc;
             a.tiles_x = tiles_x;
+            fill_fp32_constants(a);
         }
         std::vector<BatchItem> &lst = is3 ? b->host_items3 : b->host_items2;
         int local = 0;

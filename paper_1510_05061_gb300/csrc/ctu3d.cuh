@@ -150,10 +150,14 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
     const bool own = gx < nx && gy < ny;
     const int own_off = gy * nx + gx;
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
-    const T gam = T(a.gamma);
-    const T igm1 = T(1.0 / (a.gamma - 1.0));
-    const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(a.inv_dx[2])};
-    const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(a.grav[2])};
+    const T gam = arg_t<T>(a.gamma, a.gamma_f);
+    const T igm1 = arg_t<T>(1.0 / (a.gamma - 1.0), a.igm1_f);
+    const T inv_dx[3] = {arg_t<T>(a.inv_dx[0], a.inv_dx_f[0]),
+                          arg_t<T>(a.inv_dx[1], a.inv_dx_f[1]),
+                          arg_t<T>(a.inv_dx[2], a.inv_dx_f[2])};
+    const T grav[3] = {arg_t<T>(a.grav[0], a.grav_f[0]),
+                        arg_t<T>(a.grav[1], a.grav_f[1]),
+                        arg_t<T>(a.grav[2], a.grav_f[2])};
     const T hdt_dx[3] = {hdt * inv_dx[0], hdt * inv_dx[1], hdt * inv_dx[2]};   // dt / (2 dx_e)
 
     auto P = [&](int slot, int q, int hy, int hx) -> T & { return prim[((slot * NV + q) * HY + hy) * HX + hx]; };

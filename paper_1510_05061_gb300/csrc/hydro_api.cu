@@ -237,6 +237,7 @@ StepArgs step_args(const hydro_sim *s, double t_end)
     a.U0 = nullptr;
     a.zchunk = s->zchunk;
     a.tiles_x = s->tiles_x;
+    fill_fp32_constants(a);
     return a;
 }
 

@@ -70,6 +70,15 @@ __device__ __forceinline__ float rcp_t(float b) { return __fdividef(1.0f, b); }
 __device__ __forceinline__ double div_t(double a, double b) { return a * rcp_t(b); }
 __device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
 
+// A step constant in the kernel's precision: the FP64 value, or its FP32
+// copy rounded on the host (the same value as a device-side conversion).
+template <typename T>
+__device__ __forceinline__ T arg_t(double d, float f)
+{
+    if constexpr (sizeof(T) == 4) return f;
+    else return d;
+}
+
 // x > 0 (false for +-0 and for negative values).  For doubles the test is
 // an integer test of the bit pattern, which keeps it off the FP64 pipe.
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }

@@ -58,7 +58,25 @@ struct StepArgs {
     const void *U0;     // second Runge-Kutta stage: U^n, read at the cell's own position
     int zchunk;         // planes per CTA (3D)
     int tiles_x;        // tiles along x
+    // FP32 copies of gamma, 1/(gamma-1), 1/dx and g, each rounded once on
+    // the host (fill_fp32_constants): an FP32 kernel uses them as operands
+    // instead of converting the doubles, which the compiler would otherwise
+    // redo on the FP64 pipe wherever it rematerialises them
+    float gamma_f, igm1_f;
+    float inv_dx_f[3], grav_f[3];
 };
+
+// Rounds the FP32 copies of a StepArgs' constants (the same values as a
+// device-side conversion: IEEE round to nearest of the same doubles).
+inline void fill_fp32_constants(StepArgs &a)
+{
+    a.gamma_f = static_cast<float>(a.gamma);
+    a.igm1_f = static_cast<float>(1.0 / (a.gamma - 1.0));
+    for (int d = 0; d < 3; ++d) {
+        a.inv_dx_f[d] = static_cast<float>(a.inv_dx[d]);
+        a.grav_f[d] = static_cast<float>(a.grav[d]);
+    }
+}
 
 // One item of a batched step's work list: a tile and z-chunk of one instance.
 struct BatchItem {

@@ -188,6 +188,7 @@ StepArgs slab_args(const hydro_slabs *S, const Slab &sl)
         a.bgT = S->g.precision == HYDRO_FP32 ? static_cast<const void *>(sl.bgf) : static_cast<const void *>(sl.bg);
     a.zchunk = std::min(S->zchunk, sl.nz);
     a.tiles_x = sl.tiles_x;
+    fill_fp32_constants(a);
     return a;
 }
 

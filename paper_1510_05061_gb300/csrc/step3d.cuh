@@ -154,11 +154,15 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     // 2^31 cells); 64 x 64-bit multiplies would occupy the FP64 pipe
     const int plane = static_cast<int>(a.plane);
     const T dt = T(dtd), hdt = T(0.5) * T(dtd);
-    const T gam = T(a.gamma);
-    const T igm1 = T(1.0 / (a.gamma - 1.0));
+    const T gam = arg_t<T>(a.gamma, a.gamma_f);
+    const T igm1 = arg_t<T>(1.0 / (a.gamma - 1.0), a.igm1_f);
     const PlaneBGT<T> *bgT = static_cast<const PlaneBGT<T> *>(a.bgT);
-    const T inv_dx[3] = {T(a.inv_dx[0]), T(a.inv_dx[1]), T(a.inv_dx[2])};
-    const T grav[3] = {T(a.grav[0]), T(a.grav[1]), T(a.grav[2])};
+    const T inv_dx[3] = {arg_t<T>(a.inv_dx[0], a.inv_dx_f[0]),
+                          arg_t<T>(a.inv_dx[1], a.inv_dx_f[1]),
+                          arg_t<T>(a.inv_dx[2], a.inv_dx_f[2])};
+    const T grav[3] = {arg_t<T>(a.grav[0], a.grav_f[0]),
+                        arg_t<T>(a.grav[1], a.grav_f[1]),
+                        arg_t<T>(a.grav[2], a.grav_f[2])};
 
     constexpr int HXS = S::HXS;
     auto P = [&](int slot, int q, int hy, int hx) -> T & {
