@@ -383,7 +383,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
 #pragma unroll
             for (int q = 0; q < NV; ++q) FX(b, q, cy, fi) = f[q];
         }
-        for (int i = tid; i < EX * (TY + 1); i += NT) {
+        for (int i = rotated_start<NT>(tid); i < EX * (TY + 1); i += NT) {   // second pass off warp 0
             const int cx = i % EX - 1, fj = i / EX;
             T f[NV];
             y_face(b, p, fj, cx, f);
@@ -434,7 +434,8 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
                 }
                 correct(bm, 0, 0, 1, cy, cx, dy1, hdt_dx[1], dz1, hdt_dx[2], rbc, pbc, dmz);
             }
-            for (int i = tid; i < TX * EY; i += NT) {        // y states: tile columns, rows -1..TY
+            // y states: tile columns, rows -1..TY (second pass off warp 0)
+            for (int i = rotated_start<NT>(tid); i < TX * EY; i += NT) {
                 const int cx = i % TX, cy = i / TX - 1;
                 T dx1[NV], dz1[NV];
 #pragma unroll
@@ -457,7 +458,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
 #pragma unroll
                 for (int q = 0; q < NV; ++q) FX(bm, q, cy, fi) = f[q];
             }
-            for (int i = tid; i < TX * (TY + 1); i += NT) {
+            for (int i = rotated_start<NT>(tid); i < TX * (TY + 1); i += NT) {
                 const int cx = i % TX, fj = i / TX;
                 T f[NV];
                 y_face(bm, p - 1, fj, cx, f);

@@ -79,6 +79,18 @@ __device__ __forceinline__ T arg_t(double d, float f)
     else return d;
 }
 
+// First item of a CTA-strided loop (i = start, start + NT, ...) whose items
+// past the first NT -- a second pass for a few threads -- should land on
+// warps 2, 3, ... instead of 0, 1, ...: each SM sub-partition (warp mod 4)
+// has its own FP64 unit and issue slot, and when two loops of a phase both
+// leave their second pass on warp 0, that sub-partition is the critical
+// path.  Covers the same items as start = tid.
+template <int NT>
+__device__ __forceinline__ int rotated_start(int tid)
+{
+    return NT >= 128 ? (tid + NT - 64) % NT : tid;
+}
+
 // x > 0 (false for +-0 and for negative values).  For doubles the test is
 // an integer test of the bit pattern, which keeps it off the FP64 pipe.
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
