@@ -3,9 +3,11 @@
 //
 // Decomposition (2.5-D blocking): a CTA owns a TX x TY column of cells in the
 // x-y plane and marches up a chunk of z planes [z0, z1).  Per plane p it
-//   1. stages plane p+1 of U^n with a depth-2 x-y halo in shared memory,
-//      boundary conditions applied by index mapping, converted to
-//      primitives (a 3-plane ring: p-1, p, p+1);
+//   1. stages the next plane of U^n with a depth-2 x-y halo in shared
+//      memory, boundary conditions applied by index mapping, converted to
+//      primitives (a ring of the planes p-1, p, p+1, and where shared memory
+//      allows a spare slot for p+2, so that this staging and step 2 share
+//      one barrier interval);
 //   2. computes MC slopes and the MUSCL-Hancock half step of plane p for the
 //      cells that own a needed face: the tile plus a one-cell cross-shaped
 //      ring; x/y face states go to shared memory, the z face states of the
@@ -60,13 +62,11 @@ struct Step3DSmem {
     // halo depth and primitive ring: PLM needs cells i-2..i+2 for the faces
     // of a face neighbour (ring of planes p-1..p+1), PPM i-3..i+3 (p-2..p+2)
     static constexpr int H = RC == RECON_PPM ? 3 : 2;
-    static constexpr int NR = RC == RECON_PPM ? 5 : 3;
     static constexpr int HX = TX + 2 * H, HY = TY + 2 * H;
     // Row stride of the staged planes.  A warp of a 16-wide tile spans two
     // rows; for 4-byte values a stride = 16 (mod 32) puts them on disjoint
     // shared-memory banks.  (8-byte values take one wavefront per row.)
     static constexpr int HXS = (TX == 16 && sizeof(T) == 4) ? 48 : HX;
-    static constexpr size_t prim = (size_t)NR * NV * HY * HXS; // [NR][NV][HY][HXS]
     static constexpr size_t wx = (size_t)NV * TY * (TX + 2);   // [NV][TY][TX+2]
     static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;   // [NV][TY+2][TX]
     static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
@@ -74,7 +74,24 @@ struct Step3DSmem {
     // conserved values of the next two planes as copied from HBM
     static constexpr bool async = HYDRO_ASYNC_STAGING != 0 && AS;
     static constexpr size_t raw = async ? 2ull * NV * HX * HY : 0;   // [2][NV][HY*HX]
-    static constexpr size_t elems = prim + 2 * wx + 2 * wy + fx + fy + raw;
+    // planes the half step reads (p-1..p+1, PPM p-2..p+2), and one spare
+    // slot where it fits: the next plane is then converted into the spare
+    // slot in the same barrier interval as the half step (spare = true)
+    static constexpr int NRS = RC == RECON_PPM ? 5 : 3;
+    static constexpr size_t plane = (size_t)NV * HY * HXS;
+    static constexpr size_t rest = 2 * wx + 2 * wy + fx + fy + raw;
+    // (fits: one CTA's limit, and the tile's resident CTAs per SM, each with
+    // about 1.5 KB of reserved and static shared memory, in the SM's 228 KB).
+    // Measured on GB300: +4..+21 % for the synchronous FP32 tiles and +4 %
+    // for FP64 PPM; -5 % for the FP32 32 x 16 tile with asynchronous staging
+    // and -0.4 % for the FP64 PLM tiles, which keep the plain ring.
+    static constexpr size_t spare_bytes = ((NRS + 1) * plane + rest) * sizeof(T);
+    static constexpr int ctas = HYDRO_STEP3D_MIN_CTAS(T, TX, TY);
+    static constexpr bool spare = spare_bytes <= 226 * 1024 && ctas * (spare_bytes + 1536) <= 228 * 1024
+                               && (!async || (sizeof(T) == 8 && RC == RECON_PPM));
+    static constexpr int NR = NRS + (spare ? 1 : 0);
+    static constexpr size_t prim = (size_t)NR * plane;          // [NR][NV][HY][HXS]
+    static constexpr size_t elems = prim + rest;
     static constexpr size_t bytes = elems * sizeof(T);
     static_assert(bytes <= 226 * 1024, "shared memory of one CTA");
 };
@@ -133,8 +150,12 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     using S = Step3DSmem<T, HSE, TX, TY, RC, AS>;
     constexpr bool ASYNC = S::async;
     constexpr int HX = S::HX, HY = S::HY, H = S::H, NR = S::NR;
-    // planes staged ahead of the plane whose face states are computed
-    constexpr int LEAD = H - 1;
+    // planes staged ahead of the plane whose face states are computed: with
+    // the spare ring slot H, one more than the stencil reaches, so that
+    // staging plane p + H and the half step of plane p share one barrier
+    // interval; without it H - 1 and a barrier between the two
+    constexpr bool MERGED = S::spare;
+    constexpr int LEAD = MERGED ? H : H - 1;
     T *prim = reinterpret_cast<T *>(smem_raw);
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
@@ -312,22 +333,28 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         fetch(pz);
         store(pz);
     }
-    if constexpr (ASYNC) {
-        __syncthreads();
-        fetch(z0 + LEAD - 1);
-    }
+    __syncthreads();
+    if constexpr (ASYNC) fetch(z0 + LEAD - 1);
     for (int p = z0 - 1; p <= z1; ++p) {
+        // Phase 1: convert plane p+LEAD into its ring slot, then compute the
+        // half step of plane p.  MERGED: no barrier between the two (the
+        // half step reads the planes p-1..p+1 (PPM p-2..p+2), staged in
+        // earlier iterations, not the slot being filled), nor before them
+        // (the update of plane p-1 ending the previous iteration touches
+        // neither the ring nor the face states).
+        // (the last plane any half step reads is z1 + H - 1: the stencil's
+        // reach above plane z1)
         if constexpr (ASYNC) {
             // plane p+LEAD was requested one iteration ago; request the next
-            // one into the buffer the previous plane used (converted before
-            // the last barrier)
-            store(p + LEAD);
-            if (p + LEAD + 1 <= z1 + LEAD) fetch(p + LEAD + 1);
-        } else {
+            // one into the buffer the previous plane used (each thread
+            // converts the elements it copied itself)
+            if (p + LEAD <= z1 + H - 1) store(p + LEAD);
+            if (p + LEAD + 1 <= z1 + H - 1) fetch(p + LEAD + 1);
+        } else if (p + LEAD <= z1 + H - 1) {
             fetch(p + LEAD);
             store(p + LEAD);
         }
-        __syncthreads();
+        if constexpr (!MERGED) __syncthreads();
         const bool xy = (p >= z0 && p < z1);
         // the plane completed at the end of this iteration is p-1: start its
         // own-cell loads now so that they overlap the half step and fluxes
