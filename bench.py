@@ -519,7 +519,7 @@ def run_served(args):
                          "kernel": "step3d_batch_kernel<float> + step2d_batch_kernel<float>",
                          "note": "algorithmic bytes over busy (tick) time"},
             "busy_zone_updates_per_s": stats["busy_zone_updates_per_s"],
-            "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
+            "cpu_baseline": None, "e2e": None, "gpu_launches": stats["launches"], "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
     return 0

@@ -227,6 +227,7 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         prefetch = PayloadPrefetcher(requests, self.precision) if any(r.prob is None for r in requests) else None
         finished: List[Request] = []
+        launches0 = hydro.load().hydro_batch_launch_count(self.h)
         t0 = time.perf_counter()
         while pending or self.active:
             now = time.perf_counter() - t0
@@ -261,6 +262,7 @@ class Server:
             "busy_zone_updates_per_s": self.zone_updates / self.busy_s if self.busy_s else None,
             "busy_hbm_gbs": self.bytes_moved / self.busy_s / 1e9 if self.busy_s else None,
             "ticks": self.ticks,
+            "launches": hydro.load().hydro_batch_launch_count(self.h) - launches0,
         }
 
     def close(self):
