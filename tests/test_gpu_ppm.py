@@ -122,6 +122,17 @@ def test_ppm_tile_and_chunk_invariance(hy, variant, zchunk):
     assert np.array_equal(base, other)
 
 
+@pytest.mark.parametrize("variant,zchunk", [(0, 0), (3, 7), (2, 40)])
+def test_ppm_fp32_tile_and_chunk_invariance(hy, variant, zchunk):
+    """FP32 PPM stages: the 32 x 16 tile (spare ring slot) and the 32 x 8 and
+    16 x 16 tiles (no spare slot) give the same bits."""
+    prob, W = inputs.kelvin_helmholtz(35, ndim=3, U=1.2, ratio=2.0, precision=inputs.FP32)
+    prob = ppm(prob)
+    base = gpu(hy, prob, W, steps=4)["sim"].get_state()
+    other = gpu(hy, prob, W, steps=4, variant=variant, zchunk=zchunk)["sim"].get_state()
+    assert np.array_equal(base, other)
+
+
 def test_ppm_rejected_combinations(hy):
     prob, W = inputs.sod(16)
     with pytest.raises(hy.HydroError):

@@ -137,6 +137,23 @@ def test_rk2_tile_and_chunk_invariance(hy, variant, zchunk):
     assert np.array_equal(sim.get_state(), ref_state)
 
 
+@pytest.mark.parametrize("variant,zchunk", [(0, 0), (2, 5), (3, 64)])
+def test_rk2_fp32_tile_and_chunk_invariance(hy, variant, zchunk):
+    """FP32 stages: tiles whose staged-plane ring has a spare slot (staging
+    and half step in one barrier interval) and tiles without it give the
+    same bits."""
+    prob, W = inputs.rayleigh_taylor(40, nz=30, amplitude=0.05, hse_subtract=1, precision=inputs.FP32)
+    prob = prob.replace(scheme=SSPRK2)
+    base = hy.Simulation(prob, W)
+    base.run_steps(4)
+    ref_state = base.get_state()
+    base.close()
+    sim = hy.Simulation(prob, W)
+    sim.configure(variant, zchunk)
+    sim.run_steps(4)
+    assert np.array_equal(sim.get_state(), ref_state)
+
+
 def test_rk2_fp32_rayleigh_taylor_against_fp64_oracle(hy, orc):
     prob, W = inputs.rayleigh_taylor(32, amplitude=0.05, hse_subtract=1)
     p32 = prob.replace(scheme=SSPRK2, precision=inputs.FP32)
