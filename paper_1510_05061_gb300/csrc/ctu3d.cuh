@@ -505,8 +505,8 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             const T gp = gam * pres;
             const T cs = gp * rsqrt_t(gp * rho);
             const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
-            if (!(rho > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
-            else smax = fmax(smax, s);
+            if (!positive(rho) || !positive(pres) || !isfinite(s)) bad = true;
+            else smax = max_t(smax, s);
         }
         if (p >= z0) {
 #pragma unroll
