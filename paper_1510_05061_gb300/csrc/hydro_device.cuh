@@ -184,6 +184,10 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
                                         T gam, const T (&grav)[3], const CellBG<T> &bg)
 {
     constexpr int NV = ND + 2;
+    // the background enters the positivity tests in HSE mode; in plain mode
+    // the FP64 path skips the addition of its zero (0 + x is not folded for
+    // doubles), the FP32 path keeps its measured instruction schedule
+    constexpr bool BGADD = HSE || sizeof(T) == 4;
     const T rho = HSE ? bg.rho + w[0] : w[0];
     const T pr = HSE ? bg.p + w[NV - 1] : w[NV - 1];
     const T rinv = rcp_t(rho);
@@ -229,10 +233,10 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     for (int d = 0; d < ND; ++d) {
         T rb_lo = bg.rho, rb_hi = bg.rho, pb_lo = bg.p, pb_hi = bg.p;
         if (HSE && d == 2) { rb_lo = bg.rho_lo; rb_hi = bg.rho_hi; pb_lo = bg.p_lo; pb_hi = bg.p_hi; }
-        const T r_lo = rb_lo + (wh[0] - T(0.5) * dw[d][0]);
-        const T r_hi = rb_hi + (wh[0] + T(0.5) * dw[d][0]);
-        const T p_lo = pb_lo + (wh[NV - 1] - T(0.5) * dw[d][NV - 1]);
-        const T p_hi = pb_hi + (wh[NV - 1] + T(0.5) * dw[d][NV - 1]);
+        const T r_lo = BGADD ? rb_lo + (wh[0] - T(0.5) * dw[d][0]) : (wh[0] - T(0.5) * dw[d][0]);
+        const T r_hi = BGADD ? rb_hi + (wh[0] + T(0.5) * dw[d][0]) : (wh[0] + T(0.5) * dw[d][0]);
+        const T p_lo = BGADD ? pb_lo + (wh[NV - 1] - T(0.5) * dw[d][NV - 1]) : (wh[NV - 1] - T(0.5) * dw[d][NV - 1]);
+        const T p_hi = BGADD ? pb_hi + (wh[NV - 1] + T(0.5) * dw[d][NV - 1]) : (wh[NV - 1] + T(0.5) * dw[d][NV - 1]);
         ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
     }
     if (!ok) {
@@ -255,15 +259,19 @@ template <typename T, int ND, bool HSE>
 __device__ __forceinline__ void mol_faces(const T (&w)[ND + 2], T (&dw)[ND][ND + 2], const CellBG<T> &bg)
 {
     constexpr int NV = ND + 2;
+    // the background enters the positivity tests in HSE mode; in plain mode
+    // the FP64 path skips the addition of its zero (0 + x is not folded for
+    // doubles), the FP32 path keeps its measured instruction schedule
+    constexpr bool BGADD = HSE || sizeof(T) == 4;
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         T rb_lo = bg.rho, rb_hi = bg.rho, pb_lo = bg.p, pb_hi = bg.p;
         if (HSE && d == 2) { rb_lo = bg.rho_lo; rb_hi = bg.rho_hi; pb_lo = bg.p_lo; pb_hi = bg.p_hi; }
-        const T r_lo = rb_lo + (w[0] - T(0.5) * dw[d][0]);
-        const T r_hi = rb_hi + (w[0] + T(0.5) * dw[d][0]);
-        const T p_lo = pb_lo + (w[NV - 1] - T(0.5) * dw[d][NV - 1]);
-        const T p_hi = pb_hi + (w[NV - 1] + T(0.5) * dw[d][NV - 1]);
+        const T r_lo = BGADD ? rb_lo + (w[0] - T(0.5) * dw[d][0]) : (w[0] - T(0.5) * dw[d][0]);
+        const T r_hi = BGADD ? rb_hi + (w[0] + T(0.5) * dw[d][0]) : (w[0] + T(0.5) * dw[d][0]);
+        const T p_lo = BGADD ? pb_lo + (w[NV - 1] - T(0.5) * dw[d][NV - 1]) : (w[NV - 1] - T(0.5) * dw[d][NV - 1]);
+        const T p_hi = BGADD ? pb_hi + (w[NV - 1] + T(0.5) * dw[d][NV - 1]) : (w[NV - 1] + T(0.5) * dw[d][NV - 1]);
         ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
     }
     if (!ok) {
