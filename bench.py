@@ -717,7 +717,10 @@ def run_gpu(args):
     # staging depth (the tuned one for the MUSCL-Hancock step, the
     # precision's default for the stages)
     async_flag = int(variant >= 4) if not rk2 else int(itemsize == 8)
-    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}>"
+    # the FP64 MUSCL-Hancock step with gravity along z only takes the kernel
+    # without the x and y gravity terms
+    gz = int(itemsize == 8 and not rk2 and (prob.hse_subtract or (prob.grav[0] == 0 and prob.grav[1] == 0)))
+    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}, {gz}>"
                if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
     if prob.scheme == inputs.CTU:
         knames = [f"ctu3d_kernel<{tname}, {prob.hse_subtract}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3

@@ -178,7 +178,7 @@ __device__ __forceinline__ CellBG<T> cell_bg(const PlaneBGT<T> *bg, int k)
 // S(w) is gravity on the velocities.  On return dw holds the slopes used
 // (all zero after the positivity fallback) and the face states are
 // wh -/+ dw_d / 2.  Returns true when the fallback was taken.
-template <typename T, int ND, bool HSE>
+template <typename T, int ND, bool HSE, bool GZ = false>
 __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2],
                                         T (&wh)[ND + 2], T hdt, const T (&inv_dx)[3],
                                         T gam, const T (&grav)[3], const CellBG<T> &bg)
@@ -222,8 +222,11 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
         rate[4] -= wz * bg.dp * inv_dx[2];
         gsrc[2] -= bg.B * rinv;
     }
+    // (GZ: gravity along the last axis only -- the other axes' zero terms
+    // are not added)
 #pragma unroll
-    for (int d = 0; d < ND; ++d) rate[1 + d] += gsrc[d];
+    for (int d = 0; d < ND; ++d)
+        if (!GZ || d == ND - 1) rate[1 + d] += gsrc[d];
 #pragma unroll
     for (int q = 0; q < NV; ++q) wh[q] = w[q] + hdt * rate[q];
 
@@ -247,7 +250,8 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
 #pragma unroll
         for (int q = 0; q < NV; ++q) wh[q] = w[q];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) wh[1 + d] += hdt * gsrc[d];
+        for (int d = 0; d < ND; ++d)
+            if (!GZ || d == ND - 1) wh[1 + d] += hdt * gsrc[d];
     }
     return !ok;
 }

@@ -139,8 +139,10 @@ __device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chu
 // take the gravity source on the momentum from the stage's own density.
 // RC selects the face states: MC-limited linear (RECON_PLM), or piecewise
 // parabolic (RECON_PPM, Runge-Kutta stages without background only).
+// GZ: gravity along z only (g_x = g_y = 0); the x and y gravity terms, all
+// zero, are left out (their FP64 additions of zeros are not folded).
 template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM,
-          bool AS = (sizeof(T) == 8)>
+          bool AS = (sizeof(T) == 8), bool GZ = false>
 __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chunk, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
@@ -281,7 +283,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         }
         const CellBG<T> bg = cell_bg<T, HSE>(bgT, p);
         if constexpr (ST == STAGE_HANCOCK) {
-            hancock<T, ND, HSE>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
+            hancock<T, ND, HSE, GZ>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
         } else {
             mol_faces<T, ND, HSE>(w, dw, bg);
 #pragma unroll
@@ -622,7 +624,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             T du[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) du[q] = -(div_prev[q] + (fz[q] - fz_prev[q]) * inv_dx[2]);
-            const T msrc = msrc_prev + grav[2] * T(0.5) * (fz_prev[0] + fz[0]);
+            const T msrc = GZ ? grav[2] * T(0.5) * (fz_prev[0] + fz[0])
+                              : msrc_prev + grav[2] * T(0.5) * (fz_prev[0] + fz[0]);
             const T r_old = u[0];
             const T r_new = r_old + dt * du[0];
             u[0] = r_new;
@@ -631,9 +634,13 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             const T rsum = ST == STAGE_HANCOCK ? T(0.5) * (r_old + r_new) : r_old;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                T src = grav[d] * rsum;
-                if (HSE && d == 2) src -= bgB;
-                u[1 + d] += dt * (du[1 + d] + src);
+                if (GZ && d < 2) {
+                    u[1 + d] += dt * du[1 + d];
+                } else {
+                    T src = grav[d] * rsum;
+                    if (HSE && d == 2) src -= bgB;
+                    u[1 + d] += dt * (du[1 + d] + src);
+                }
             }
             u[4] += dt * (du[4] + msrc);
             if constexpr (ST == STAGE_RK2) {
@@ -662,8 +669,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                       + (FY(q, ty + 1, tx) - FY(q, ty, tx)) * inv_dx[1];
 #pragma unroll
             for (int q = 0; q < NV; ++q) div_prev[q] = dv[q];
-            msrc_prev = grav[0] * T(0.5) * (FX(0, ty, tx) + FX(0, ty, tx + 1))
-                      + grav[1] * T(0.5) * (FY(0, ty, tx) + FY(0, ty + 1, tx));
+            if constexpr (!GZ)
+                msrc_prev = grav[0] * T(0.5) * (FX(0, ty, tx) + FX(0, ty, tx + 1))
+                          + grav[1] * T(0.5) * (FY(0, ty, tx) + FY(0, ty + 1, tx));
         }
 #pragma unroll
         for (int q = 0; q < NV; ++q) { ztop_prev[q] = ztop[q]; fz_prev[q] = fz[q]; }
@@ -672,7 +680,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 }
 
 template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM,
-          bool AS = (sizeof(T) == 8)>
+          bool AS = (sizeof(T) == 8), bool GZ = false>
 __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) step3d_kernel(const StepArgs a)
 {
     constexpr int NT = TX * TY;
@@ -694,7 +702,7 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
-    step3d_body<T, HSE, TX, TY, ST, RC, AS>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
         // the intermediate state only raises error bits; dt and time move

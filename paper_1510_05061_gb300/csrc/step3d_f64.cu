@@ -8,10 +8,10 @@ namespace hydro {
 
 namespace {
 
-template <typename T, bool HSE, int TX, int TY, bool AS>
-cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
+template <typename T, bool HSE, int TX, int TY, bool AS, bool GZ>
+cudaError_t launch3d_g(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
-    auto k = step3d_kernel<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS>;
+    auto k = step3d_kernel<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS, GZ>;
     constexpr size_t smem = Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes;
     static bool configured = false;   // the attribute is per function
     if (!configured) {
@@ -21,6 +21,19 @@ cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
     }
     k<<<grid, TX * TY, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// Gravity along z only (always so with the hydrostatic background) takes the
+// kernel without the x and y gravity terms.
+template <typename T, bool HSE, int TX, int TY, bool AS>
+cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
+{
+    if constexpr (HSE) {
+        return launch3d_g<T, HSE, TX, TY, AS, true>(a, grid, s);
+    } else {
+        if (a.grav[0] == 0.0 && a.grav[1] == 0.0) return launch3d_g<T, HSE, TX, TY, AS, true>(a, grid, s);
+        return launch3d_g<T, HSE, TX, TY, AS, false>(a, grid, s);
+    }
 }
 
 template <bool HSE>
