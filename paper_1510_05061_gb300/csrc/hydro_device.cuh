@@ -178,10 +178,11 @@ __device__ __forceinline__ CellBG<T> cell_bg(const PlaneBGT<T> *bg, int k)
 // S(w) is gravity on the velocities.  On return dw holds the slopes used
 // (all zero after the positivity fallback) and the face states are
 // wh -/+ dw_d / 2.  Returns true when the fallback was taken.
-template <typename T, int ND, bool HSE, bool GZ = false>
+template <typename T, int ND, bool HSE, bool GZ = false, bool RINV = false>
 __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2],
                                         T (&wh)[ND + 2], T hdt, const T (&inv_dx)[3],
-                                        T gam, const T (&grav)[3], const CellBG<T> &bg)
+                                        T gam, const T (&grav)[3], const CellBG<T> &bg,
+                                        T rinv_given = T(0))
 {
     constexpr int NV = ND + 2;
     // the background enters the positivity tests in HSE mode; in plain mode
@@ -190,7 +191,8 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     constexpr bool BGADD = HSE || sizeof(T) == 4;
     const T rho = HSE ? bg.rho + w[0] : w[0];
     const T pr = HSE ? bg.p + w[NV - 1] : w[NV - 1];
-    const T rinv = rcp_t(rho);
+    // RINV: 1/rho as computed when the cell was staged (the same value)
+    const T rinv = RINV ? rinv_given : rcp_t(rho);
     const T gp = gam * pr;
     T rate[NV];
 #pragma unroll

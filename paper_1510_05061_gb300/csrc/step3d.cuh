@@ -78,7 +78,11 @@ struct Step3DSmem {
     // slot where it fits: the next plane is then converted into the spare
     // slot in the same barrier interval as the half step (spare = true)
     static constexpr int NRS = RC == RECON_PPM ? 5 : 3;
-    static constexpr size_t plane = (size_t)NV * HY * HXS;
+    // staged arrays per plane: the primitives, and for FP64 PLM also 1/rho
+    // (computed by the conversion anyway; the half step then needs no FP64
+    // reciprocal of its own)
+    static constexpr int NVS = (sizeof(T) == 8 && RC == RECON_PLM) ? NV + 1 : NV;
+    static constexpr size_t plane = (size_t)NVS * HY * HXS;
     static constexpr size_t rest = 2 * wx + 2 * wy + fx + fy + raw;
     // (fits: one CTA's limit, and the tile's resident CTAs per SM, each with
     // about 1.5 KB of reserved and static shared memory, in the SM's 228 KB).
@@ -189,8 +193,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                         arg_t<T>(a.grav[2], a.grav_f[2])};
 
     constexpr int HXS = S::HXS;
+    constexpr int NVS = S::NVS;
     auto P = [&](int slot, int q, int hy, int hx) -> T & {
-        return prim[((slot * NV + q) * HY + hy) * HXS + hx];   // 32-bit shared-memory indices
+        return prim[((slot * NVS + q) * HY + hy) * HXS + hx];   // 32-bit shared-memory indices
     };
 
     // ---- stage plane pz (may be a ghost plane) into its ring slot, in two
@@ -265,6 +270,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                 P(slot, 2, hy, hx) = m1 * rinv;
                 P(slot, 3, hy, hx) = m2 * rinv;
                 P(slot, 4, hy, hx) = (gam - T(1)) * (v[4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+                if constexpr (NVS > NV) P(slot, NV, hy, hx) = rinv;
             }
         }
     };
@@ -283,7 +289,10 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         }
         const CellBG<T> bg = cell_bg<T, HSE>(bgT, p);
         if constexpr (ST == STAGE_HANCOCK) {
-            hancock<T, ND, HSE, GZ>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
+            if constexpr (NVS > NV)
+                hancock<T, ND, HSE, GZ, true>(w, dw, wh, hdt, inv_dx, gam, grav, bg, P(s0, NV, hy, hx));
+            else
+                hancock<T, ND, HSE, GZ>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
         } else {
             mol_faces<T, ND, HSE>(w, dw, bg);
 #pragma unroll
