@@ -112,6 +112,27 @@ CONFIGS = {
 }
 
 
+def step_kernel_names(prob, variant: int):
+    """The kernels of one step of `prob` with 3D tile variant `variant`, as
+    the profiler prints their names (the keys of profiles/traffic.json)."""
+    itemsize = 4 if prob.precision == inputs.FP32 else 8
+    rk2 = prob.scheme == inputs.SSPRK2
+    tile = TILE_NAMES.get(variant, "32, 8") if prob.ndim == 3 else "32, 8"
+    tname = "double" if itemsize == 8 else "float"
+    stages = (1, 2) if rk2 else (0,)
+    # template arguments: stage, reconstruction, staging depth (the tuned one
+    # for the MUSCL-Hancock step, the precision's default for the stages),
+    # and whether the FP64 MUSCL-Hancock step takes the kernel for gravity
+    # along z only (without the x and y gravity terms)
+    async_flag = int(variant >= 4) if not rk2 else int(itemsize == 8)
+    gz = int(itemsize == 8 and not rk2 and bool(prob.hse_subtract or (prob.grav[0] == 0 and prob.grav[1] == 0)))
+    if prob.scheme == inputs.CTU:
+        return [f"ctu3d_kernel<{tname}, {prob.hse_subtract}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3
+                else f"ctu2d_kernel<{tname}, 32, 8>"]
+    return [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}, {gz}>"
+             if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
+
+
 def kernel_source_sha() -> str:
     """Hash of the CUDA sources: measured traffic is valid only for the
     kernels it was taken from."""
@@ -166,6 +187,8 @@ def record_traffic(config: str, csv_path: str) -> int:
     except (OSError, ValueError):
         table = {}
     sha = kernel_source_sha()
+    # entries of this workload taken from other sources are stale: drop them
+    table[config] = {k: v for k, v in table.get(config, {}).items() if v.get("source_sha") == sha}
     rows = []
     total_ns = 0.0
     for name, launches in per.items():
@@ -710,21 +733,7 @@ def run_gpu(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     clocks = clk.summary()
     variant = tune["variant"] if tune else (0 if itemsize == 4 else 4)
-    tile = TILE_NAMES.get(variant, "32, 8") if prob.ndim == 3 else "32, 8"
-    tname = "double" if itemsize == 8 else "float"
-    stages = (1, 2) if rk2 else (0,)
-    # template arguments as the profiler prints them: stage, reconstruction,
-    # staging depth (the tuned one for the MUSCL-Hancock step, the
-    # precision's default for the stages)
-    async_flag = int(variant >= 4) if not rk2 else int(itemsize == 8)
-    # the FP64 MUSCL-Hancock step with gravity along z only takes the kernel
-    # without the x and y gravity terms
-    gz = int(itemsize == 8 and not rk2 and (prob.hse_subtract or (prob.grav[0] == 0 and prob.grav[1] == 0)))
-    knames = [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}, {gz}>"
-               if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
-    if prob.scheme == inputs.CTU:
-        knames = [f"ctu3d_kernel<{tname}, {prob.hse_subtract}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3
-                  else f"ctu2d_kernel<{tname}, 32, 8>"]
+    knames = step_kernel_names(prob, variant)
     kname = " + ".join(knames)
     # DRAM bytes of one step: the sum over its kernels (null if any is missing or stale)
     traffic = args.traffic

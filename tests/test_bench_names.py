@@ -1,0 +1,59 @@
+"""Host-side checks of bench.py's profiler kernel names: the keys under which
+profiles/traffic.json stores each workload's measured DRAM traffic must be
+the names bench.py derives for the kernels it times."""
+
+import json
+import os
+
+import pytest
+
+import bench
+from paper_1510_05061_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def small(cfg):
+    """The workload's problem at a small size (names do not depend on n)."""
+    c = bench.CONFIGS[cfg]
+    prob, _ = inputs.rayleigh_taylor(8, precision=c["precision"], hse_subtract=c["hse"])
+    return prob.replace(scheme=c.get("scheme", inputs.HANCOCK), recon=c.get("recon", inputs.PLM))
+
+
+def test_fp64_step_with_gravity_along_z_takes_the_specialised_kernel():
+    prob = small("rt256-fp64")
+    assert bench.step_kernel_names(prob, 6) == ["step3d_kernel<double, 0, 16, 16, 0, 0, 1, 1>"]
+    # gravity with an x component: the general kernel
+    assert bench.step_kernel_names(prob.replace(grav=(0.1, 0.0, -1.0)), 6) == \
+        ["step3d_kernel<double, 0, 16, 16, 0, 0, 1, 0>"]
+    # the background mode always has gravity along z only
+    assert bench.step_kernel_names(small("rt256-fp64-hse"), 2) == ["step3d_kernel<double, 1, 16, 16, 0, 0, 0, 1>"]
+
+
+def test_fp32_stage_and_ctu_names():
+    assert bench.step_kernel_names(small("rt512-fp32"), 7) == ["step3d_kernel<float, 1, 32, 16, 0, 0, 1, 0>"]
+    assert bench.step_kernel_names(small("rt512-fp32-rk2"), 0) == [
+        "step3d_kernel<float, 1, 32, 8, 1, 0, 0, 0>", "step3d_kernel<float, 1, 32, 8, 2, 0, 0, 0>"]
+    assert bench.step_kernel_names(small("rt256-fp64-ppm"), 6) == [
+        "step3d_kernel<double, 0, 16, 16, 1, 1, 1, 0>", "step3d_kernel<double, 0, 16, 16, 2, 1, 1, 0>"]
+    assert bench.step_kernel_names(small("rt256-fp64-ctu"), 0) == ["ctu3d_kernel<double, 0, 16, 8>"]
+    assert bench.step_kernel_names(small("rt512-fp32-ctu"), 0) == ["ctu3d_kernel<float, 1, 16, 16>"]
+
+
+def test_recorded_traffic_keys_are_names_bench_derives():
+    """Every step-kernel entry taken from the current sources is a name the
+    bench derives (so bench.py finds it and reports it as roofline.traffic)."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        table = json.load(fh)
+    sha = bench.kernel_source_sha()
+    checked = 0
+    for cfg, kernels in table.items():
+        c = bench.CONFIGS.get(cfg)
+        if c is None or c.get("batch") or c.get("served") or c.get("slabs"):
+            continue
+        derived = {n for v in range(8) for n in bench.step_kernel_names(small(cfg), v)}
+        for k, e in kernels.items():
+            if k.startswith(("step3d_kernel", "ctu3d_kernel")) and e.get("source_sha") == sha:
+                assert k in derived, (cfg, k)
+                checked += 1
+    assert checked >= 8
