@@ -57,3 +57,20 @@ def test_recorded_traffic_keys_are_names_bench_derives():
                 assert k in derived, (cfg, k)
                 checked += 1
     assert checked >= 8
+
+
+def test_profile_commands_name_existing_workloads():
+    """The commands quoted in profiles/*.md run committed files only: every
+    --config they name is a bench.py workload."""
+    import glob
+    import re
+
+    names = set()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as fh:
+            names |= set(re.findall(r"--config\s+([A-Za-z0-9_.-]+)", fh.read()))
+    names -= {"<cfg>", "$c"}
+    names = {n for n in names if not n.startswith(("<", "$"))}
+    assert names, "no workload named in the profiles"
+    missing = sorted(n for n in names if n not in bench.CONFIGS)
+    assert not missing, missing
