@@ -108,7 +108,7 @@ typedef struct {
     double grav[3];
     int precision;       /* HYDRO_FP64 or HYDRO_FP32 */
     int hse_subtract;
-    int scheme;          /* HYDRO_SCHEME_HANCOCK (0) or HYDRO_SCHEME_SSPRK2 */
+    int scheme;          /* HYDRO_SCHEME_HANCOCK (0), HYDRO_SCHEME_SSPRK2 or HYDRO_SCHEME_CTU */
     int recon;           /* HYDRO_RECON_PLM (0) or HYDRO_RECON_PPM */
 } hydro_problem;
 
@@ -133,6 +133,18 @@ size_t hydro_workspace_bytes(const hydro_problem *prob);
    first dt on the device; t = 0, step = 0.  *out receives the handle. */
 int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work,
                const double *W0, const double *bg, void *stream, hydro_sim **out);
+
+/* hydro_init with the initial state given as HOST FP64 total conserved
+   variables U0 = (rho, rho u_0 .. rho u_{ndim-1}, E), nvar planes of
+   nx*ny*nz values.  The device rounds them to the stored precision (FP32
+   for HYDRO_FP32) and, with hse_subtract, first subtracts the background
+   U0(z) = (rho0, 0, 0, 0, p0/(gamma-1)) in FP64.  Every other argument,
+   the set-up and the errors are those of hydro_init.  (hydro_init takes
+   primitives because initial conditions are specified as density,
+   velocity and pressure at cell centres; this entry serves restarts and
+   couplings that hold conserved variables.) */
+int hydro_init_conserved(const hydro_problem *prob, void *Ua, void *Ub, void *work,
+                         const double *U0, const double *bg, void *stream, hydro_sim **out);
 
 /* One step on the handle's stream.  dt_taken (nullable): when given, the
    call synchronises and returns the dt used; when NULL nothing is read back
@@ -199,6 +211,20 @@ int hydro_checkpoint_load(hydro_sim *sim, const char *path);
    the stream. */
 int hydro_selftest_math(int which, const double *x, const double *y, double *out, long n,
                         void *stream);
+
+/* Test hook, needs no GPU: drives the per-device one-time set-up guards
+   that the kernel launchers use (kernel attributes such as the
+   shared-memory limit, and occupancy-derived persistent grid sizes, are
+   per device, so one process driving several devices must configure each)
+   with a fake sequence of device ordinals devs[0..n) in [0, ndev) instead
+   of real devices, walked by `threads` host threads at once.  The set-up
+   for device fail_dev (-1: none) fails on its first attempt and must be
+   retried.  On return once_calls[d] and value_calls[d] count the set-up
+   attempts for device d of the run-once guard and of the cached-value
+   guard, and values[d] holds the cached value (100 + d once computed).
+   Returns HYDRO_ERR_STATE if a thread saw a wrong cached value. */
+int hydro_selftest_device_once(const int *devs, int n, int fail_dev, int threads, int ndev,
+                               int *once_calls, int *value_calls, int *values);
 
 int hydro_destroy(hydro_sim *sim);
 const char *hydro_strerror(int status);
@@ -288,16 +314,18 @@ int hydro_batch_destroy(hydro_batch *b);
    HYDRO_RED_TOTALS (out[q] = sum over cells of the total conserved variable q
    times the cell volume, q < ndim + 2) for the state U (device pointer, the
    layout and precision of prob; with hse_subtract the stored perturbation,
-   and bg the HOST background tables in hydro_init's order).  Its scratch is
-   one fixed array of about 420 KB in device memory, part of the library
-   image: every GPU that loads the library holds it until the process exits.
-   Limits: hse problems need nz + 5 <= 4096; larger ones are rejected with
-   HYDRO_ERR_INVALID_ARG before anything is launched.  The first call on each
-   device looks up the array's device address (with that device current);
-   make that first call before any stream capture.  All calls share the one
-   array: calls whose work overlaps on the GPU (other streams or threads)
-   race and give wrong sums; calls on one stream are ordered.  Runs on
-   `stream` and synchronises it; calls no allocating routine. */
+   and bg the HOST background tables in hydro_init's order, which must be
+   finite).  Its scratch is one fixed array of about 420 KB in device memory,
+   part of the library image: every GPU that loads the library holds it
+   until the process exits.  Limits: hse problems need nz + 5 <= 4096;
+   larger ones are rejected with HYDRO_ERR_INVALID_ARG before anything is
+   launched.  Every call looks up the array's device address on the current
+   device, copies the background from pageable host memory and synchronises
+   `stream`, so it cannot be called while a stream is being captured.  All
+   calls share the one array: calls whose GPU work can overlap race and give
+   wrong sums -- calls on different streams, and calls from different host
+   threads even on one stream (their clears, kernels and read-backs can
+   interleave).  Calls no allocating routine. */
 int hydro_totals_noalloc(const hydro_problem *prob, const void *U, const double *bg,
                          void *stream, double *out);
 

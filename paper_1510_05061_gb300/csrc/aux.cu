@@ -22,18 +22,24 @@ __global__ void init_convert_kernel(const AuxArgs a, const double *__restrict__ 
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
          i += (long long)gridDim.x * blockDim.x) {
         const long long c = c0 + i;
-        const double rho = W[i];
-        double ke = 0.0;
         double u[NV];
-        u[0] = rho;
+        if (a.conserved_in) {
+            // total conserved variables as given
 #pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            const double v = W[(1 + d) * m + i];
-            u[1 + d] = rho * v;
-            ke += v * v;
+            for (int q = 0; q < NV; ++q) u[q] = W[q * m + i];
+        } else {
+            const double rho = W[i];
+            double ke = 0.0;
+            u[0] = rho;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const double v = W[(1 + d) * m + i];
+                u[1 + d] = rho * v;
+                ke += v * v;
+            }
+            const double p = W[(NV - 1) * m + i];
+            u[NV - 1] = p / (a.gamma - 1.0) + 0.5 * rho * ke;
         }
-        const double p = W[(NV - 1) * m + i];
-        u[NV - 1] = p / (a.gamma - 1.0) + 0.5 * rho * ke;
         if (HSE) {
             const int k = (int)(c / a.plane);
             u[0] -= a.bg[k + 2].rho_c;

@@ -1,56 +1,36 @@
 // batch3d_f64.cu -- FP64 instantiations of the persistent batched 3D step
 // for every tile shape the autotuner may choose, both modes.
 #include "launchers.h"
+#include "per_device.h"
 #include "step3d.cuh"
 
 namespace hydro {
 
 namespace {
 
-int sm_count()
-{
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
-template <typename K>
-cudaError_t prepare(K kernel, size_t smem, int threads, int *max_grid)
-{
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
-    if (e != cudaSuccess) return e;
-    *max_grid = (nb > 0 ? nb : 1) * sm_count();
-    return cudaSuccess;
-}
-
 template <typename T, bool HSE, int TX, int TY, bool AS>
 struct Batch3D {
-    static int &grid_cap() { static int g = 0; return g; }
-    static cudaError_t ensure()
+    static cudaError_t ensure(int *grid)
     {
-        if (grid_cap()) return cudaSuccess;
-        return prepare(step3d_batch_kernel<T, HSE, TX, TY, AS>, Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes,
-                       TX * TY,
-                       &grid_cap());
+        static PerDeviceInt cache;   // per device: shared-memory limit and resident grid
+        return persistent_grid(cache, step3d_batch_kernel<T, HSE, TX, TY, AS>,
+                               Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes, TX * TY, grid);
     }
     static cudaError_t launch(const BatchInst *insts, const BatchItem *items, int nitems, int parity,
                               int grid, cudaStream_t s)
     {
-        cudaError_t e = ensure();
+        int cap = 0;
+        cudaError_t e = ensure(&cap);
         if (e != cudaSuccess) return e;
         step3d_batch_kernel<T, HSE, TX, TY, AS>
             <<<grid, TX * TY, Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes, s>>>(insts, items, nitems, parity);
         return cudaGetLastError();
     }
-    static int max_grid() { return ensure() == cudaSuccess ? grid_cap() : 0; }
+    static int max_grid()
+    {
+        int cap = 0;
+        return ensure(&cap) == cudaSuccess ? cap : 0;
+    }
 };
 
 template <bool HSE>

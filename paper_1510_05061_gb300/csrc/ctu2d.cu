@@ -2,6 +2,7 @@
 // upwind step.
 #include "ctu2d.cuh"
 #include "launchers.h"
+#include "per_device.h"
 
 namespace hydro {
 
@@ -11,12 +12,9 @@ static cudaError_t launch_ctu(const StepArgs &a, dim3 grid, cudaStream_t s)
     constexpr int TX = STEP2D_TX, TY = STEP2D_TY;
     auto k = ctu2d_kernel<T, TX, TY>;
     constexpr size_t smem = Ctu2DSmem<T, TX, TY>::bytes;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static PerDeviceOnce configured;   // the attribute is per function and device
+    const cudaError_t e = ensure_smem_limit(configured, k, smem);
+    if (e != cudaSuccess) return e;
     k<<<grid, TX * TY, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -6,6 +6,7 @@
 
 #include "ctu3d.cuh"
 #include "launchers.h"
+#include "per_device.h"
 
 namespace hydro {
 
@@ -28,12 +29,9 @@ cudaError_t launch_ctu(const StepArgs &a0, cudaStream_t s)
 {
     auto k = ctu3d_kernel<T, HSE, TX, TY>;
     constexpr size_t smem = Ctu3DSmem<T, TX, TY>::bytes;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static PerDeviceOnce configured;   // the attribute is per function and device
+    const cudaError_t e = ensure_smem_limit(configured, k, smem);
+    if (e != cudaSuccess) return e;
     StepArgs a = a0;
     a.tiles_x = (a.n[0] + TX - 1) / TX;
     a.zchunk = ctu_zchunk(a.n, sizeof(T) == 4);

@@ -11,11 +11,13 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/hydro.h"
 #include "hydro_internal.h"
 #include "launchers.h"
+#include "per_device.h"
 
 using namespace hydro;
 
@@ -339,10 +341,15 @@ size_t hydro_workspace_bytes(const hydro_problem *prob)
     return layout(prob).total;
 }
 
-int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const double *W0,
-               const double *bg, void *stream, hydro_sim **out)
+}  // extern "C"
+
+namespace {
+
+// hydro_init and hydro_init_conserved: host0 holds total primitive
+// (conserved = false) or total conserved (conserved = true) FP64 variables.
+int init_impl(const hydro_problem *prob, void *Ua, void *Ub, void *work, const double *W0,
+              const double *bg, void *stream, hydro_sim **out, bool conserved)
 {
-    ApiRange range("hydro_init");
     if (!out) return HYDRO_ERR_INVALID_ARG;
     *out = nullptr;
     int rc = check_problem(prob);
@@ -430,6 +437,7 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
     }
 
     AuxArgs a = aux_args(s, s->buf[s->cur]);
+    a.conserved_in = conserved ? 1 : 0;
     rc = staged_upload(s, W0, [&](long long c0, long long m, double *stg) {
         s->launches += 1;
         return cuda_status(launch_init_convert(a, stg, c0, m, s->stream));
@@ -440,6 +448,24 @@ int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const 
     if (rc != HYDRO_OK) { delete s; return rc; }
     *out = s;
     return c.err ? HYDRO_ERR_NONPHYSICAL : HYDRO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_init(const hydro_problem *prob, void *Ua, void *Ub, void *work, const double *W0,
+               const double *bg, void *stream, hydro_sim **out)
+{
+    ApiRange range("hydro_init");
+    return init_impl(prob, Ua, Ub, work, W0, bg, stream, out, false);
+}
+
+int hydro_init_conserved(const hydro_problem *prob, void *Ua, void *Ub, void *work, const double *U0,
+                         const double *bg, void *stream, hydro_sim **out)
+{
+    ApiRange range("hydro_init_conserved");
+    return init_impl(prob, Ua, Ub, work, U0, bg, stream, out, true);
 }
 
 int hydro_step(hydro_sim *s, double *dt_taken)
@@ -656,6 +682,47 @@ int hydro_selftest_math(int which, const double *x, const double *y, double *out
     cudaError_t e = launch_math(which, x, y, out, n, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return cuda_status(e);
+}
+
+int hydro_selftest_device_once(const int *devs, int n, int fail_dev, int threads, int ndev,
+                               int *once_calls, int *value_calls, int *values)
+{
+    if (!devs || n < 0 || threads < 1 || threads > 64 || ndev < 1 || ndev > MAX_DEVICES || !once_calls ||
+        !value_calls || !values)
+        return HYDRO_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (devs[i] < 0 || devs[i] >= ndev) return HYDRO_ERR_INVALID_ARG;
+    PerDeviceOnce once;
+    PerDeviceInt cache;
+    std::vector<std::atomic<int>> oc(ndev), vc(ndev);
+    for (int d = 0; d < ndev; ++d) { oc[d] = 0; vc[d] = 0; values[d] = 0; }
+    std::atomic<int> bad{0};
+    auto walk = [&] {
+        for (int i = 0; i < n; ++i) {
+            const int d = devs[i];
+            // the set-up of fail_dev fails on its first attempt and must be retried
+            const cudaError_t e = once.run(d, [&] {
+                const int attempt = oc[d].fetch_add(1);
+                return (d == fail_dev && attempt == 0) ? cudaErrorUnknown : cudaSuccess;
+            });
+            int v = 0;
+            const cudaError_t f = cache.get(d, [&](int *out) {
+                const int attempt = vc[d].fetch_add(1);
+                if (d == fail_dev && attempt == 0) return cudaErrorUnknown;
+                *out = 100 + d;
+                return cudaSuccess;
+            }, &v);
+            if (f == cudaSuccess && v != 100 + d) bad.fetch_add(1);
+            if (f == cudaSuccess) values[d] = v;
+            (void)e;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(walk);
+    walk();
+    for (auto &th : pool) th.join();
+    for (int d = 0; d < ndev; ++d) { once_calls[d] = oc[d]; value_calls[d] = vc[d]; }
+    return bad.load() ? HYDRO_ERR_STATE : HYDRO_OK;
 }
 
 int hydro_destroy(hydro_sim *s)

@@ -95,10 +95,17 @@ __device__ __forceinline__ int rotated_start(int tid)
 // an integer test of the bit pattern, which keeps it off the FP64 pipe.
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
-// Sign tests for the HLLC fan branches: x >= 0 and x <= 0, by sign bit for
-// doubles (a signed zero may fall on either side; the flux is continuous
-// across both branch boundaries, so this only moves rounding).
-__device__ __forceinline__ bool nonnegative(double x) { return __double_as_longlong(x) >= 0; }
+// Sign tests for the HLLC fan branches: x >= 0 and x <= 0 as numeric
+// comparisons (both zeros satisfy both), done on the bit pattern for doubles:
+// x >= 0 holds for a clear sign bit and for -0 (whose pattern is the most
+// negative 64-bit integer); x <= 0 holds for a set sign bit and for +0.
+// A wave speed S* of -0 (reached at reflecting walls, where the two states
+// are mirror images) therefore takes the left branch, as S* = +0 does.
+__device__ __forceinline__ bool nonnegative(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == (long long)0x8000000000000000ull;
+}
 __device__ __forceinline__ bool nonnegative(float x) { return x >= 0.0f; }
 __device__ __forceinline__ bool nonpositive(double x) { return __double_as_longlong(x) <= 0; }
 __device__ __forceinline__ bool nonpositive(float x) { return x <= 0.0f; }

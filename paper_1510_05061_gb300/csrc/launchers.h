@@ -79,9 +79,11 @@ struct AuxArgs {
     double *partial;      // per-CTA partials (max_ctas * 5 doubles)
     const PlaneBG *bg;    // hse tables or nullptr
     int hse, fp32;
+    int conserved_in;     // init conversion: staging holds conserved (1) or primitive (0) variables
 };
 
-// staging (FP64 primitives of cells [c0, c0 + m), planes of length m) -> state
+// staging (FP64 total primitive, or with a.conserved_in total conserved,
+// variables of cells [c0, c0 + m), planes of length m) -> stored state
 cudaError_t launch_init_convert(const AuxArgs &a, const double *staging, long long c0,
                                 long long m, cudaStream_t s);
 // max signal speed of the state -> ctrl->dt_next (time unchanged)

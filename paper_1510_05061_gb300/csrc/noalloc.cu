@@ -5,12 +5,11 @@
 // per-CTA partial sums and the background table) lives in one file-scope
 // __device__ array of fixed size instead of a caller workspace.  The host
 // needs that array's device address: in host code the symbol name only
-// stands in for it, so the address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// stands in for it, so every call looks the address up on the current
+// device with cudaGetSymbolAddress.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/hydro.h"
 #include "hydro_internal.h"
@@ -35,24 +34,15 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = (sizeof(NoallocScratch) + 255) / 256 * 
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 128;
-std::mutex setup_mutex;
-void *scratch_addr[MAX_DEVICES] = {nullptr};
-
-// Device address of the scratch on the current device (set-up on the first
-// call per device, with that device current).
+// Device address of the scratch on the current device.  Looked up on every
+// call (cudaGetSymbolAddress allocates nothing): a cached address could
+// outlive the context it belongs to (after cudaDeviceReset, or when the
+// primary context is released and created again).
 int scratch_for_current_device(NoallocScratch **out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return HYDRO_ERR_CUDA;
-    if (dev < 0 || dev >= MAX_DEVICES) return HYDRO_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(setup_mutex);
-    if (!scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return HYDRO_ERR_CUDA;
-        scratch_addr[dev] = p;
-    }
-    *out = static_cast<NoallocScratch *>(scratch_addr[dev]);
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return HYDRO_ERR_CUDA;
+    *out = static_cast<NoallocScratch *>(p);
     return HYDRO_OK;
 }
 
@@ -64,7 +54,12 @@ extern "C" int hydro_totals_noalloc(const hydro_problem *prob, const void *U, co
     if (!prob || !U || !out) return HYDRO_ERR_INVALID_ARG;
     if (hydro_state_bytes(prob) == 0) return HYDRO_ERR_INVALID_ARG;
     const int nz = prob->n[2];
-    if (prob->hse_subtract && (nz + 5 > NOALLOC_MAX_BG_PLANES || !bg)) return HYDRO_ERR_INVALID_ARG;
+    if (prob->hse_subtract) {
+        if (nz + 5 > NOALLOC_MAX_BG_PLANES || !bg) return HYDRO_ERR_INVALID_ARG;
+        // the four tables (2 (nz + 4) centre and 2 (nz + 5) face entries) must be finite
+        for (int i = 0; i < 4 * nz + 18; ++i)
+            if (!std::isfinite(bg[i])) return HYDRO_ERR_INVALID_ARG;
+    }
     const long long plane = (long long)prob->n[0] * prob->n[1];
     const long long N = plane * nz;
     if (5 * aux_reduce_blocks(N) > NOALLOC_MAX_PARTIALS) return HYDRO_ERR_INVALID_ARG;

@@ -1,6 +1,7 @@
 // step2d.cu -- FP64 and FP32 instantiations of the fused 2D step and of
 // the two Runge-Kutta stages.
 #include "launchers.h"
+#include "per_device.h"
 #include "step2d.cuh"
 
 namespace hydro {
@@ -11,12 +12,9 @@ static cudaError_t launch2d(const StepArgs &a, dim3 grid, cudaStream_t s)
     constexpr int TX = STEP2D_TX, TY = STEP2D_TY;
     auto k = step2d_kernel<T, TX, TY, ST, RC>;
     constexpr size_t smem = Step2DSmem<T, TX, TY, RC>::bytes;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static PerDeviceOnce configured;   // the attribute is per function and device
+    const cudaError_t e = ensure_smem_limit(configured, k, smem);
+    if (e != cudaSuccess) return e;
     k<<<grid, TX * TY, smem, s>>>(a);
     return cudaGetLastError();
 }

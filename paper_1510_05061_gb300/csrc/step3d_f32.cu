@@ -2,6 +2,7 @@
 // for every tile shape and
 // staging depth.
 #include "launchers.h"
+#include "per_device.h"
 #include "step3d.cuh"
 
 namespace hydro {
@@ -13,12 +14,9 @@ cudaError_t launch3d(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
     auto k = step3d_kernel<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS>;
     constexpr size_t smem = Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes;
-    static bool configured = false;   // the attribute is per function
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static PerDeviceOnce configured;   // the attribute is per function and device
+    const cudaError_t e = ensure_smem_limit(configured, k, smem);
+    if (e != cudaSuccess) return e;
     k<<<grid, TX * TY, smem, s>>>(a);
     return cudaGetLastError();
 }

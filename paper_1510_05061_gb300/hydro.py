@@ -41,11 +41,11 @@ HYDRO_RED_DT_LAST = 6
 
 # every symbol include/hydro.h declares
 EXPORTS = (
-    "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_step",
+    "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_init_conserved", "hydro_step",
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
     "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk", "hydro_set_tile",
     "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
-    "hydro_selftest_math", "hydro_batch_workspace_bytes", "hydro_batch_init",
+    "hydro_selftest_math", "hydro_selftest_device_once", "hydro_batch_workspace_bytes", "hydro_batch_init",
     "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
     "hydro_batch_create", "hydro_batch_add", "hydro_batch_remove", "hydro_batch_set_graph",
     "hydro_batch_configure", "hydro_batch_variant_shape", "hydro_batch_step", "hydro_batch_reduce",
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
     L.hydro_workspace_bytes.argtypes = [P]
     L.hydro_init.restype = C.c_int
     L.hydro_init.argtypes = [P, vp, vp, vp, D, D, vp, C.POINTER(vp)]
+    L.hydro_init_conserved.restype = C.c_int
+    L.hydro_init_conserved.argtypes = [P, vp, vp, vp, D, D, vp, C.POINTER(vp)]
     L.hydro_step.restype = C.c_int
     L.hydro_step.argtypes = [vp, D]
     L.hydro_advance_to.restype = C.c_int
@@ -120,6 +122,8 @@ def load(path: str = LIB_PATH):
     L.hydro_strerror.argtypes = [C.c_int]
     L.hydro_selftest_math.restype = C.c_int
     L.hydro_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_long, vp]
+    L.hydro_selftest_device_once.restype = C.c_int
+    L.hydro_selftest_device_once.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     PP = C.POINTER(C.c_void_p)
     L.hydro_batch_workspace_bytes.restype = C.c_size_t
     L.hydro_batch_workspace_bytes.argtypes = [P, C.c_int]
@@ -259,6 +263,17 @@ def hydro_init(prob: hydro_problem, Ua: int, Ub: int, work: int, W0: np.ndarray,
     return h
 
 
+def hydro_init_conserved(prob: hydro_problem, Ua: int, Ub: int, work: int, U0: np.ndarray,
+                         bg: Optional[np.ndarray], stream: int) -> C.c_void_p:
+    h = C.c_void_p()
+    rc = load().hydro_init_conserved(C.byref(prob), C.c_void_p(Ua), C.c_void_p(Ub), C.c_void_p(work),
+                                     _dptr(U0), _dptr(bg), C.c_void_p(stream), C.byref(h))
+    if rc != HYDRO_OK and h.value:
+        load().hydro_destroy(h)
+    _check(rc, "hydro_init_conserved")
+    return h
+
+
 def hydro_step(h, want_dt: bool = False) -> Optional[float]:
     dt = C.c_double(0.0)
     _check(load().hydro_step(h, C.byref(dt) if want_dt else None), "hydro_step")
@@ -312,6 +327,19 @@ def hydro_selftest_math(which: int, x: int, y: int, out: int, n: int, stream: in
                                       int(n), C.c_void_p(stream)), "hydro_selftest_math")
 
 
+def hydro_selftest_device_once(devs, fail_dev: int = -1, threads: int = 1, ndev: int = 4):
+    """(once_calls, value_calls, values) per fake device (see include/hydro.h)."""
+    d = np.ascontiguousarray(devs, dtype=np.int32)
+    once = np.zeros(ndev, np.int32)
+    vcalls = np.zeros(ndev, np.int32)
+    vals = np.zeros(ndev, np.int32)
+    ip = C.POINTER(C.c_int)
+    _check(load().hydro_selftest_device_once(d.ctypes.data_as(ip), d.size, int(fail_dev), int(threads),
+                                             int(ndev), once.ctypes.data_as(ip), vcalls.ctypes.data_as(ip),
+                                             vals.ctypes.data_as(ip)), "hydro_selftest_device_once")
+    return once, vcalls, vals
+
+
 def hydro_destroy(h):
     _check(load().hydro_destroy(h), "hydro_destroy")
 
@@ -331,11 +359,13 @@ class Simulation:
     """One solve: torch-owned device buffers bound to a libhydro handle.
 
     W0 is the host FP64 array of total primitive fields (rho, u.., p) of
-    shape prob.shape.  Runs on ``stream`` (a torch.cuda.Stream) or on the
-    current stream of the current device.
+    shape prob.shape, or with ``conserved=True`` of total conserved fields
+    (rho, m.., E) (hydro_init_conserved).  Runs on ``stream`` (a
+    torch.cuda.Stream) or on the current stream of the current device.
     """
 
-    def __init__(self, prob: "inputs.Problem", W0: np.ndarray, stream=None, device=None):
+    def __init__(self, prob: "inputs.Problem", W0: np.ndarray, stream=None, device=None,
+                 conserved: bool = False):
         import torch
 
         if not torch.cuda.is_available():
@@ -358,8 +388,8 @@ class Simulation:
             raise ValueError(f"W0 shape {self._W0.shape} != {prob.shape}")
         self._bg = background_tables(prob)
         with torch.cuda.device(dev):
-            self.h = hydro_init(self.cp, ptrs[0], ptrs[1], ptrs[2], self._W0, self._bg,
-                                self.stream.cuda_stream)
+            init = hydro_init_conserved if conserved else hydro_init
+            self.h = init(self.cp, ptrs[0], ptrs[1], ptrs[2], self._W0, self._bg, self.stream.cuda_stream)
 
     # stepping ---------------------------------------------------------
     def step(self, want_dt: bool = False):

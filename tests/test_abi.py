@@ -114,3 +114,43 @@ def test_background_table_order(hy):
     assert t.size == 2 * 20 + 2 * 21
     np.testing.assert_array_equal(t[:20], prob.bg_rho_c)
     np.testing.assert_array_equal(t[40:61], prob.bg_rho_f)
+
+
+def test_per_device_setup_runs_once_per_device(hy):
+    """The launchers' attribute/occupancy set-up is kept per device ordinal:
+    one process driving several devices configures each of them once, a
+    failed set-up is retried, and concurrent host threads do not repeat it."""
+    devs = [0, 1, 0, 1, 1, 0, 2, 3, 2, 0]
+    once, vcalls, vals = hy.hydro_selftest_device_once(devs, ndev=4)
+    assert once.tolist() == [1, 1, 1, 1]
+    assert vcalls.tolist() == [1, 1, 1, 1]
+    assert vals.tolist() == [100, 101, 102, 103]
+    # a device never seen is never configured
+    once, vcalls, vals = hy.hydro_selftest_device_once([0, 2, 2], ndev=4)
+    assert once.tolist() == [1, 0, 1, 0] and vals.tolist() == [100, 0, 102, 0]
+    # device 1's first set-up fails: its next use retries it, the others are unaffected
+    once, vcalls, vals = hy.hydro_selftest_device_once(devs, fail_dev=1, ndev=4)
+    assert once.tolist() == [1, 2, 1, 1] and vcalls.tolist() == [1, 2, 1, 1]
+    assert vals.tolist() == [100, 101, 102, 103]
+    # eight host threads walking the same devices at once
+    for _ in range(20):
+        once, vcalls, vals = hy.hydro_selftest_device_once(devs * 10, threads=8, ndev=4)
+        assert once.tolist() == [1, 1, 1, 1] and vcalls.tolist() == [1, 1, 1, 1]
+        assert vals.tolist() == [100, 101, 102, 103]
+    with pytest.raises(hy.HydroError):
+        hy.hydro_selftest_device_once([5], ndev=4)
+
+
+def test_conserved_init_argument_checks(hy):
+    from paper_1510_05061_gb300 import inputs
+
+    prob, W = inputs.sod(16)
+    cp = hy.make_problem(prob)
+    h = C.c_void_p()
+    # a missing initial state and a null output are refused before any CUDA call
+    assert hy.load().hydro_init_conserved(C.byref(cp), C.c_void_p(256), C.c_void_p(512),
+                                          C.c_void_p(1024), None, None, None,
+                                          C.byref(h)) == hy.HYDRO_ERR_INVALID_ARG
+    assert hy.load().hydro_init_conserved(C.byref(cp), C.c_void_p(256), C.c_void_p(512),
+                                          C.c_void_p(1024), W.ctypes.data_as(C.POINTER(C.c_double)),
+                                          None, None, None) == hy.HYDRO_ERR_INVALID_ARG

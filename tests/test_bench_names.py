@@ -41,21 +41,32 @@ def test_fp32_stage_and_ctu_names():
 
 
 def test_recorded_traffic_keys_are_names_bench_derives():
-    """Every step-kernel entry taken from the current sources is a name the
-    bench derives (so bench.py finds it and reports it as roofline.traffic)."""
+    """Every recorded step-kernel entry of the latest capture is a name the
+    bench derives, so that bench.py finds it and reports it as
+    roofline.traffic while the kernel sources still hash to the captured ones
+    (entries of other sources are reported as null traffic)."""
+    import collections
+
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
         table = json.load(fh)
-    sha = bench.kernel_source_sha()
-    checked = 0
+    entries = []
     for cfg, kernels in table.items():
         c = bench.CONFIGS.get(cfg)
         if c is None or c.get("batch") or c.get("served") or c.get("slabs"):
             continue
-        derived = {n for v in range(8) for n in bench.step_kernel_names(small(cfg), v)}
         for k, e in kernels.items():
-            if k.startswith(("step3d_kernel", "ctu3d_kernel")) and e.get("source_sha") == sha:
-                assert k in derived, (cfg, k)
-                checked += 1
+            if k.startswith(("step3d_kernel", "ctu3d_kernel")):
+                entries.append((cfg, k, e.get("source_sha")))
+    shas = collections.Counter(sha for _, _, sha in entries)
+    current = bench.kernel_source_sha()
+    latest = current if current in shas else shas.most_common(1)[0][0]
+    checked = 0
+    for cfg, k, sha in entries:
+        if sha != latest:
+            continue
+        derived = {n for v in range(8) for n in bench.step_kernel_names(small(cfg), v)}
+        assert k in derived, (cfg, k)
+        checked += 1
     assert checked >= 8
 
 

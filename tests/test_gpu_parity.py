@@ -394,3 +394,30 @@ def test_tile_shape_invariance_bitwise(hy, prec, variants):
         with pytest.raises(hy.HydroError):
             sim.set_tile(3)          # the 512-thread tile is FP32 only
         sim.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp64_hse", "fp32_hse"])
+def test_init_from_conserved_matches_init_from_primitives(hy, orc, mode):
+    """hydro_init_conserved with the total conserved variables of an initial
+    state gives the stored state hydro_init gives from its primitives (up to
+    the rounding of the conversion) and the same run."""
+    prec = inputs.FP32 if mode == "fp32" or mode.startswith("fp32") else inputs.FP64
+    prob, W = inputs.rayleigh_taylor(20, nz=24, amplitude=0.05, hse_subtract=int("hse" in mode),
+                                     precision=prec)
+    o = orc.Oracle(prob.replace(precision=inputs.FP64))
+    Utot = o.total(o.state_from_prim(W))          # total conserved, FP64, computed on the host
+    a = hy.Simulation(prob, W)
+    b = hy.Simulation(prob, Utot, conserved=True)
+    Sa, Sb = a.get_state(), b.get_state()
+    if prec == inputs.FP64:
+        np.testing.assert_allclose(Sb, Sa, rtol=1e-13, atol=1e-13 * np.abs(Sa).max())
+    else:
+        # the two FP64 values round to the same float or to neighbouring floats
+        np.testing.assert_allclose(Sb, Sa, rtol=2.5e-7, atol=1e-7 * np.abs(Sa).max())
+    assert abs(a.dt - b.dt) <= 1e-12 * a.dt
+    a.run_steps(3)
+    b.run_steps(3)
+    tol = TOL if prec == inputs.FP64 else 1e-5
+    assert_parity(b.conserved(), a.conserved(), tol=tol, label=mode)
+    a.close()
+    b.close()

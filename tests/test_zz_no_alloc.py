@@ -63,11 +63,19 @@ def test_noalloc_totals_match_workspace_totals(hy, name, make):
 
 
 def test_noalloc_rejects_oversized_background(hy):
+    import torch
+
     prob, _ = inputs.rayleigh_taylor(4, nz=5000, perturb=False, hse_subtract=1)
     cp = hy.make_problem(prob)
     bg = hy.background_tables(prob)
+    # a real device buffer of the problem's state size: should the size check
+    # ever regress, the call still reads only memory it was given
+    nbytes = hy.load().hydro_state_bytes(C.byref(cp))
+    assert nbytes > 0
+    U = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
     out = np.zeros(5)
-    rc = hy.load().hydro_totals_noalloc(C.byref(cp), C.c_void_p(1 << 20),
+    rc = hy.load().hydro_totals_noalloc(C.byref(cp), C.c_void_p(U.data_ptr()),
                                         bg.ctypes.data_as(C.POINTER(C.c_double)), None,
                                         out.ctypes.data_as(C.POINTER(C.c_double)))
+    torch.cuda.synchronize()
     assert rc == hy.HYDRO_ERR_INVALID_ARG
