@@ -102,6 +102,10 @@ def lib():
             L.orc_exact_sample.restype = None
             L.orc_exact_sample.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double,
                                            C.c_double, _D]
+            L.orc_fallback_counts.restype = None
+            L.orc_fallback_counts.argtypes = [C.POINTER(C.c_longlong), C.c_int]
+            L.orc_face_states.restype = C.c_int
+            L.orc_face_states.argtypes = [P, _D, C.c_double, _D, C.POINTER(C.c_ubyte)]
             L.orc_exact_profile.restype = C.c_int
             L.orc_exact_profile.argtypes = [_D, _D, C.c_double, C.c_double, C.c_double, _D,
                                             C.c_long, _D, _D, _D]
@@ -187,6 +191,21 @@ class Oracle:
             raise FloatingPointError(f"oracle step failed ({rc})")
         return V
 
+    def face_states(self, U: np.ndarray, dt: float):
+        """(Wf, mask): the face states the integrator predicts from U with
+        time step dt, Wf[d, s, q] of shape state-shape[1:] (s = 0 the low
+        face; stored form, i.e. perturbations in hse mode), and the cells
+        that took the positivity fallback."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        nd, nv = self.prob.ndim, self.prob.nvar
+        Wf = np.zeros((nd, 2, nv) + tuple(U.shape[1:]), dtype=np.float64)
+        mask = np.zeros(U.shape[1:], dtype=np.uint8)
+        rc = self.L.orc_face_states(C.byref(self.p), _ptr(U), float(dt), _ptr(Wf),
+                                    mask.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        if rc:
+            raise ValueError(f"oracle rejected the problem ({rc})")
+        return Wf, mask.astype(bool)
+
     def run(self, U: np.ndarray, t_end: float = float("inf"), max_steps: int = 1 << 40,
             t0: float = 0.0, record_dt: bool = False):
         """Advance a copy of U; returns (U, t, steps, dt_last[, dts])."""
@@ -203,6 +222,15 @@ class Oracle:
         if record_dt:
             return V, t.value, s.value, dl.value, dts[: s.value].copy()
         return V, t.value, s.value, dl.value
+
+
+def fallback_counts(reset: bool = True):
+    """(cells, pairs) since the last reset: interior cells whose face states
+    took the positivity fallback, and corner transport upwind cell-axis pairs
+    kept uncorrected (test instrumentation; no effect on results)."""
+    out = (C.c_longlong * 2)()
+    lib().orc_fallback_counts(out, 1 if reset else 0)
+    return int(out[0]), int(out[1])
 
 
 # single-face helpers for unit tests ------------------------------------------

@@ -406,11 +406,18 @@ typedef struct {
     double *Wf;     /* face states, [d][side][q]; side 0 = low face  2*ndim*nvar */
     double *F;      /* fluxes through the high face of each cell, [d][q] */
     double *F1;     /* corner transport upwind: first-pass fluxes, [d][q] */
+    unsigned char *fb;  /* 1 where a cell's face states took the positivity fallback */
 } work_t;
+
+/* Test instrumentation (no effect on any result): interior cells whose face
+   states took the positivity fallback (slopes zeroed), and cell-axis pairs
+   of the corner transport upwind step kept uncorrected, summed over every
+   step since the last orc_fallback_counts(.., 1). */
+static long long fallback_cells = 0, ctu_uncorrected_pairs = 0;
 
 static void work_free(work_t *w)
 {
-    free(w->G); free(w->W); free(w->dW); free(w->Wf); free(w->F); free(w->F1);
+    free(w->G); free(w->W); free(w->dW); free(w->Wf); free(w->F); free(w->F1); free(w->fb);
     memset(w, 0, sizeof(*w));
 }
 
@@ -425,6 +432,8 @@ static int work_alloc(const orc_params *p, work_t *w)
     w->dW = (double *)calloc((size_t)nd * nv, a);
     w->Wf = (double *)calloc((size_t)2 * nd * nv, a);
     w->F = (double *)calloc((size_t)nd * nv, a);
+    w->fb = (unsigned char *)calloc((size_t)w->g.npad, 1);
+    if (!w->fb) { work_free(w); return ERR_OOM; }
     if (p->scheme == SCHEME_CTU) {
         w->F1 = (double *)calloc((size_t)nd * nv, a);
         if (!w->F1) { work_free(w); return ERR_OOM; }
@@ -514,7 +523,8 @@ static void ctu_correct(const orc_params *p, work_t *wk, double dt)
         }
         clo[d] -= 1;
         chi[d] += 1;
-        #pragma omp parallel for collapse(2) schedule(static)
+        long long kept = 0;
+        #pragma omp parallel for collapse(2) schedule(static) reduction(+ : kept)
         for (int kk = clo[2]; kk < chi[2]; ++kk)
             for (int j = clo[1]; j < chi[1]; ++j)
                 for (int i = clo[0]; i < chi[0]; ++i) {
@@ -548,10 +558,11 @@ static void ctu_correct(const orc_params *p, work_t *wk, double dt)
                         wc[s][0] -= rb;
                         wc[s][nd + 1] -= pb;
                     }
-                    if (bad) continue;
+                    if (bad) { ++kept; continue; }
                     for (int s = 0; s < 2; ++s)
                         for (int q = 0; q < nv; ++q) wk->Wf[((d * 2 + s) * nv + q) * np + c] = wc[s][q];
                 }
+        ctu_uncorrected_pairs += kept;
     }
 }
 
@@ -559,13 +570,12 @@ static void ctu_correct(const orc_params *p, work_t *wk, double dt)
    the MUSCL-Hancock step; MODE_STAGE: one forward-Euler stage U + dt L(U)
    of the method of lines (face states W -/+ dW/2, gravity on the momentum
    from the stage density); MODE_CTU: the corner transport upwind step. */
-static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int mode)
+static void predict_faces(const orc_params *p, work_t *wk, const double *U, double dt, int mode)
 {
     const int predictor = mode != MODE_STAGE;
     const grid_t *g = &wk->g;
     const int nd = g->ndim, nv = g->nvar;
     const long np = g->npad;
-    const long N = (long)g->n[0] * g->n[1] * g->n[2];
     const double gam = p->gamma;
     const int st[3] = {1, g->P[0], g->P[0] * g->P[1]};   /* padded strides */
 
@@ -616,7 +626,8 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
        at once, then face states W +- dW/2 (or PPM's) with the per-cell
        fallback */
     const double hdt = 0.5 * dt;
-    #pragma omp parallel for collapse(2) schedule(static)
+    long long nfb = 0;
+    #pragma omp parallel for collapse(2) schedule(static) reduction(+ : nfb)
     for (int kk = flo_c[2]; kk < fhi_c[2]; ++kk)
         for (int j = flo_c[1]; j < fhi_c[1]; ++j) {
             int k = zplane(g, kk);
@@ -725,8 +736,27 @@ static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int 
                     for (int s = 0; s < 2; ++s)
                         for (int q = 0; q < nv; ++q)
                             wk->Wf[((d * 2 + s) * nv + q) * np + c] = wf[d][s][q];
+                wk->fb[c] = (unsigned char)bad;
+                if (bad && i >= g->ng[0] && i < g->ng[0] + g->n[0] && j >= g->ng[1] &&
+                    j < g->ng[1] + g->n[1] && kk >= g->ng[2] && kk < g->ng[2] + g->n[2])
+                    ++nfb;
             }
         }
+    fallback_cells += nfb;
+}
+
+static int step_with(const orc_params *p, work_t *wk, double *U, double dt, int mode)
+{
+    const int predictor = mode != MODE_STAGE;
+    const grid_t *g = &wk->g;
+    const int nd = g->ndim, nv = g->nvar;
+    const long np = g->npad;
+    const long N = (long)g->n[0] * g->n[1] * g->n[2];
+    const double gam = p->gamma;
+    const int st[3] = {1, g->P[0], g->P[0] * g->P[1]};
+
+    /* 1.-4. ghosts, primitives, slopes, predicted face states */
+    predict_faces(p, wk, U, dt, mode);
 
     /* 5. HLLC flux through the high face of each cell along d, for every
        face of the interior; the corner transport upwind step first takes
@@ -979,4 +1009,52 @@ void orc_phys_flux(int ndim, double gam, int d, const double *w, double *f)
 void orc_prim_to_cons1(int ndim, double gam, const double *w, double *u)
 {
     prim_to_cons(ndim, gam, w, u);
+}
+
+/* ------------------------------------------------------------------ */
+/* test instrumentation                                                 */
+/* ------------------------------------------------------------------ */
+
+/* out[0]: interior cells whose face states took the positivity fallback,
+   out[1]: corner transport upwind cell-axis pairs kept uncorrected, both
+   summed over every step since the last reset; reset != 0 zeroes them
+   after reading. */
+void orc_fallback_counts(long long *out, int reset)
+{
+    out[0] = fallback_cells;
+    out[1] = ctu_uncorrected_pairs;
+    if (reset) fallback_cells = ctu_uncorrected_pairs = 0;
+}
+
+/* The face states the problem's integrator predicts from U with time step
+   dt (steps 1-4 of a step; for the corner transport upwind method the
+   one-dimensional predictor's states before the transverse correction; for
+   the method of lines the first stage's W -/+ dW/2), for every interior
+   cell: Wf[((d * 2 + s) * nvar + q) * N + cell], s = 0 the low face, in
+   the stored form (rho', u, p' in hse mode); mask[cell] = 1 where the cell
+   took the positivity fallback. */
+int orc_face_states(const orc_params *p, const double *U, double dt, double *Wf, unsigned char *mask)
+{
+    int rc = check_params(p);
+    if (rc) return rc;
+    work_t wk;
+    if (work_alloc(p, &wk)) return ERR_OOM;
+    const int mode = p->scheme == SCHEME_CTU ? MODE_CTU : (p->scheme == SCHEME_SSPRK2 ? MODE_STAGE : MODE_HANCOCK);
+    predict_faces(p, &wk, U, dt, mode);
+    const grid_t *g = &wk.g;
+    const int nd = g->ndim, nv = g->nvar;
+    const long np = g->npad, N = (long)g->n[0] * g->n[1] * g->n[2];
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                long c = pidx(g, i + g->ng[0], j + g->ng[1], k + g->ng[2]);
+                long o = ((long)k * g->n[1] + j) * g->n[0] + i;
+                for (int d = 0; d < nd; ++d)
+                    for (int s = 0; s < 2; ++s)
+                        for (int q = 0; q < nv; ++q)
+                            Wf[((long)(d * 2 + s) * nv + q) * N + o] = wk.Wf[((d * 2 + s) * nv + q) * np + c];
+                mask[o] = wk.fb[c];
+            }
+    work_free(&wk);
+    return OK;
 }

@@ -417,3 +417,75 @@ def vortex_prim(prob: Problem, t: float, beta: float = 5.0, vel=(1.0, 1.0)) -> n
     W[2, 0] = vel[1] + amp * X
     W[3, 0] = rho ** gamma
     return W
+
+
+def riemann_tube(n: int, left, right, x0: float = 0.5, axis: int = 0, ndim: int = 2,
+                 width: int = 4, boost: float = 0.0, grav=(0.0, 0.0, 0.0),
+                 transverse_bc: int = BC_PERIODIC, gamma: float = 1.4, cfl: float = 0.8,
+                 precision: int = FP64, scheme: int = HANCOCK) -> Tuple[Problem, np.ndarray]:
+    """One-dimensional Riemann problem in a strip of n cells along `axis`
+    (length 1, split at x0) and `width` square cells across each other axis.
+
+    left/right hold (rho, u, p) with u along the strip; `boost` is added to
+    both velocities (a Galilean boost, whose exact solution is the unboosted
+    one translated by boost * t).  Outflow ends along the strip; the
+    transverse boundaries are `transverse_bc`.  Every cross-section starts
+    equal, so each row along the strip evolves as the same row.
+    """
+    n_ = [1, 1, 1]
+    hi = [1.0, 1.0, 1.0]
+    bc_lo = [BC_OUTFLOW] * 3
+    bc_hi = [BC_OUTFLOW] * 3
+    for d in range(ndim):
+        n_[d] = n if d == axis else width
+        hi[d] = 1.0 if d == axis else width / n
+        if d != axis:
+            bc_lo[d] = bc_hi[d] = transverse_bc
+    prob = Problem(ndim=ndim, n=tuple(n_), hi=tuple(hi), bc_lo=tuple(bc_lo), bc_hi=tuple(bc_hi),
+                   gamma=gamma, cfl=cfl, grav=tuple(grav), precision=precision, scheme=scheme,
+                   name=f"tube{ndim}d-{n}-axis{axis}")
+    x = prob.centres(axis)
+    shape = [1, 1, 1]
+    shape[2 - axis] = -1
+    is_left = (x < x0).reshape(shape)
+    W = _prim_zeros(prob)
+    W[0] = np.where(is_left, left[0], right[0])
+    W[1 + axis] = np.where(is_left, left[1] + boost, right[1] + boost)
+    W[-1] = np.where(is_left, left[2], right[2])
+    return prob, W
+
+
+def filament_column(nz: int = 48, nxy: int = 8, height: float = 12.0, stream: float = 3.0,
+                    hse_subtract: int = 0, precision: int = FP64, scheme: int = HANCOCK,
+                    cfl: float = 0.8) -> Tuple[Problem, np.ndarray]:
+    """Isothermal atmosphere rho0 = p0 = exp(-z) under g = -1 on
+    [0,1]^2 x [0, height] (periodic in x and y, reflecting in z), whose top
+    (above z = 2/3 height, where p0 falls to ~1e-4 .. 6e-6: near vacuum)
+    carries dense filaments streaming along x: there the density is rho0
+    times the periodic x pattern (1, 10, 40, 40, 40, 10, 1, 1) (stretched over
+    nxy cells), the pressure stays p0, v_x = stream and v_y = 0.3 sin(2 pi y).
+    The heavy filaments above the light gas and the fast stream through
+    density jumps of 40 make predicted face states non-positive in many
+    cells.  The background tables are the exact exp(-z) at centres and faces.
+    """
+    prob = Problem(ndim=3, n=(nxy, nxy, nz), hi=(1.0, 1.0, height),
+                   bc_lo=(BC_PERIODIC, BC_PERIODIC, BC_REFLECT),
+                   bc_hi=(BC_PERIODIC, BC_PERIODIC, BC_REFLECT), grav=(0.0, 0.0, -1.0),
+                   precision=precision, hse_subtract=hse_subtract, scheme=scheme, cfl=cfl,
+                   name=f"filaments-{nxy}x{nxy}x{nz}")
+    dz = prob.dx()[2]
+    zc = (np.arange(-2, nz + 2, dtype=np.float64) + 0.5) * dz
+    zf = np.arange(-2, nz + 3, dtype=np.float64) * dz
+    prob.bg_rho_c, prob.bg_p_c = np.exp(-zc), np.exp(-zc)
+    prob.bg_rho_f, prob.bg_p_f = np.exp(-zf), np.exp(-zf)
+    z = prob.centres(2)
+    y = prob.centres(1)
+    top = (z > 2.0 * height / 3.0)[:, None, None]
+    base = np.array([1.0, 10.0, 40.0, 40.0, 40.0, 10.0, 1.0, 1.0])
+    pattern = base[(np.arange(nxy) * 8) // nxy]
+    W = _prim_zeros(prob)
+    W[0] = np.exp(-z)[:, None, None] * np.where(top, pattern[None, None, :], 1.0)
+    W[4] = np.exp(-z)[:, None, None] * np.ones((1, nxy, nxy))
+    W[1] = np.where(top, stream, 0.0) * np.ones((nz, nxy, nxy))
+    W[2] = np.where(top, 0.3 * np.sin(2.0 * math.pi * y)[None, :, None], 0.0) * np.ones((nz, nxy, nxy))
+    return prob, W
