@@ -221,6 +221,43 @@ def fp64_peak_tflops(sm_mhz: float) -> float:
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def measure_fma_peak(precision: int, target_ms: float = 40.0) -> dict:
+    """Measured FMA-pipe throughput of one precision on the current device:
+    the library's probe kernel (8 CTAs of 256 threads per SM, 8 independent
+    FMA chains per thread) timed with CUDA events on its stream, best of
+    three launches of about target_ms each, with the SM clock sampled."""
+    import torch
+
+    from paper_1510_05061_gb300 import hydro
+
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctas, threads = 8 * sms, 256
+    dt = torch.float64 if precision == inputs.FP64 else torch.float32
+    out = torch.empty(ctas * threads, dtype=dt, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def timed(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        hydro.hydro_fma_probe(precision, iters, ctas, threads, out.data_ptr(), s.cuda_stream)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    iters = 2000 if precision == inputs.FP64 else 100000
+    timed(iters)
+    ms = timed(iters)
+    iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+    with ClockSampler(dev) as clk:
+        best = min(timed(iters) for _ in range(3))
+    flops = hydro.hydro_fma_probe_flops(iters, ctas, threads)
+    return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "iters": iters, "ctas": ctas,
+            "threads": threads, "clocks": clk.summary(),
+            "how": "FMA probe kernel: 8 CTAs x 256 threads per SM, 8 independent chains x <- x*a + b "
+                   "per thread, CUDA events, best of 3"}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -380,6 +417,57 @@ def oracle_sample(seconds: float = 10.0, max_steps: int = 1000, cfg="rt256-fp64"
     return prob.ncell * done / el, cores, f"{desc}, {done} oracle step(s), {el:.1f} s"
 
 
+def fp32_accuracy(cfg: str, t_end: float = 0.5) -> dict:
+    """FP32 error against the FP64 oracle: the FP32 GPU path and the oracle
+    run the workload's problem at a reduced grid (RT 64^3, 2D KH 256^2) to
+    t_end from the same seeded initial state; density L1-relative
+    difference at t_end (about 1-5 s of oracle time on 16 cores)."""
+    import oracle
+
+    from paper_1510_05061_gb300 import hydro
+
+    c = CONFIGS[cfg]
+    kind = c.get("kind", "rt")
+    if kind == "kh2d":
+        prob, W = inputs.kelvin_helmholtz(256, ndim=2, U=1.0, ratio=2.0, precision=inputs.FP32)
+    else:
+        prob, W = inputs.rayleigh_taylor(64, precision=inputs.FP32, hse_subtract=c["hse"])
+    prob = prob.replace(scheme=c.get("scheme", inputs.HANCOCK), recon=c.get("recon", inputs.PLM))
+    sim = hydro.Simulation(prob, W)
+    steps, t = sim.advance_to(t_end)
+    rho_gpu = sim.primitive()[0]
+    sim.close()
+    oracle.build()
+    o = oracle.Oracle(prob.replace(precision=inputs.FP64))
+    V, to, so, _ = o.run(o.state_from_prim(W), t_end=t_end)
+    rho = o.prim(V)[0]
+    return {"vs": "FP64 CPU oracle", "grid": list(prob.n[:prob.ndim]), "t": t_end,
+            "steps_fp32": steps, "steps_oracle": so,
+            "density_l1_rel": float(np.abs(rho_gpu - rho).sum() / np.abs(rho).sum())}
+
+
+def batch_accuracy(b, items, count: int = 4) -> dict:
+    """FP32 batch instances against the FP64 oracle: the `count` smallest
+    boxes after the steps they have taken (the oracle takes as many steps from
+    the same initial state); the largest density L1-relative difference."""
+    import oracle
+
+    oracle.build()
+    order = sorted(range(len(items)), key=lambda i: items[i][0].ncell)[:count]
+    worst, steps = 0.0, []
+    for i in order:
+        p, W = items[i]
+        n = b.nstep(i)
+        rho_gpu = b.conserved(i)[0]
+        o = oracle.Oracle(p.replace(precision=inputs.FP64))
+        V, _, s, _ = o.run(o.state_from_prim(W), max_steps=n)
+        rho = o.total(V)[0]
+        worst = max(worst, float(np.abs(rho_gpu - rho).sum() / np.abs(rho).sum()))
+        steps.append(n)
+    return {"vs": "FP64 CPU oracle, same number of steps", "instances": [items[i][0].n[0] for i in order],
+            "steps": steps, "density_l1_rel_max": worst}
+
+
 def run_reference(args):
     world, rank, local = dist_setup()
     if rank != 0:
@@ -474,6 +562,7 @@ def run_gpu_batch(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = 2 * 5 * 4 * cells / (per_launch_ms * 1e-3) / 1e9
     items3, items2, grid3, grid2 = b.items()
+    accuracy = batch_accuracy(b, items) if rank == 0 and not args.no_accuracy else None
     b.close()
     kname = f"step3d_batch_kernel<float, 0, {TILE_NAMES[tune['variant']]}, {int(tune['variant'] >= 4)}>"
     if rank == 0:
@@ -491,6 +580,7 @@ def run_gpu_batch(args):
                          "traffic": args.traffic if args.traffic is not None else measured_traffic(args.config, kname),
                          "algorithmic_bytes": 2 * 5 * 4 * cells},
             "autotune": {k: v for k, v in tune.items() if k != "table"},
+            "accuracy": accuracy,
             "cpu_baseline": None, "e2e": None,
             "gpu_launches": launches, "clocks": clk.summary(),
         }
@@ -602,7 +692,8 @@ def run_gpu_slabs(args):
     N = prob.ncell
     value = world * N * args.steps / (el_ms * 1e-3)
     peaks, peak_kind = measured_peaks()
-    peak_tf = fp64_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    fma = measure_fma_peak(inputs.FP64)
+    peak_tf = fma["tflops"]
     ach_tf = FLOPS_PER_ZONE_3D * N / (el_ms / args.steps * 1e-3) / 1e12
     if rank == 0:
         line = {
@@ -618,7 +709,8 @@ def run_gpu_slabs(args):
             "autotune": tune,
             "roofline": {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": ach_tf / peak_tf, "traffic": None,
-                         "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                         "peak_kind": "measured: FP64 FMA probe (" + fma["how"] + ")",
+                         "peak_derived": fp64_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0))),
                          "kernel": "step3d_kernel<double, 0, ...> over all slabs (whole step time)"},
             "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
         }
@@ -740,21 +832,31 @@ def run_gpu(args):
     if traffic is None:
         per = [measured_traffic(args.config, k) for k in knames]
         traffic = sum(per) if all(v is not None for v in per) else None
+    ach_tf = flops_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e12
+    fma = measure_fma_peak(prob.precision)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     if prob.precision == inputs.FP64:
-        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak_tf = fp64_peak_tflops(sm_mhz)
-        ach_tf = flops_per_zone * zones_per_launch / (kern_avg_ms * 1e-3) / 1e12
+        peak_tf = fma["tflops"]
         roofline = {"bound": "alu", "achieved": ach_tf, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": ach_tf / peak_tf, "traffic": traffic,
-                    "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock",
+                    "peak_kind": "measured: FP64 FMA probe (" + fma["how"] + ")",
+                    "peak_derived": fp64_peak_tflops(sm_mhz),
+                    "peak_probe_clocks": fma["clocks"],
                     "kernel": kname, "algorithmic_bytes": bytes_per_zone * zones_per_launch,
+                    "algorithmic_flops": flops_per_zone * zones_per_launch,
                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                             "frac": achieved_gbs / hbm_peak, "peak_kind": peak_kind}}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_gbs / hbm_peak, "traffic": traffic,
                     "peak_kind": peak_kind, "kernel": kname,
-                    "algorithmic_bytes": bytes_per_zone * zones_per_launch}
+                    "algorithmic_bytes": bytes_per_zone * zones_per_launch,
+                    "alu": {"achieved": ach_tf, "peak": fma["tflops"], "unit": "TFLOP/s",
+                            "frac": ach_tf / fma["tflops"],
+                            "peak_kind": "measured: FP32 FMA probe (" + fma["how"] + ")"}}
+    accuracy = None
+    if prob.precision == inputs.FP32 and rank == 0 and not args.no_accuracy:
+        accuracy = fp32_accuracy(args.config)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -778,6 +880,7 @@ def run_gpu(args):
             "kernel_ms_avg": kern_avg_ms,
             "autotune": tune,
             "roofline": roofline,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -834,6 +937,8 @@ def main():
     ap.add_argument("--config", default="rt256-fp64", choices=sorted(CONFIGS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="FP32 workloads: skip the error against the FP64 oracle")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the step kernel from an ncu capture")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")

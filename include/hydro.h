@@ -226,6 +226,17 @@ int hydro_selftest_math(int which, const double *x, const double *y, double *out
 int hydro_selftest_device_once(const int *devs, int n, int fail_dev, int threads, int ndev,
                                int *once_calls, int *value_calls, int *values);
 
+/* Throughput probe of the fused multiply-add pipe of one precision
+   (HYDRO_FP64 or HYDRO_FP32), the denominator of the step kernels'
+   arithmetic roofline: `ctas` CTAs of `threads` threads (a multiple of 32,
+   at most 256) each run 8 independent chains x <- x * a + b for `iters`
+   rounds and store their sums into `out` (device, ctas * threads values of
+   the precision).  Launches on `stream` without synchronising: the caller
+   times it with events.  hydro_fma_probe_flops gives the floating-point
+   operations of one launch (2 per FMA). */
+int hydro_fma_probe(int precision, long long iters, int ctas, int threads, void *out, void *stream);
+double hydro_fma_probe_flops(long long iters, int ctas, int threads);
+
 int hydro_destroy(hydro_sim *sim);
 const char *hydro_strerror(int status);
 

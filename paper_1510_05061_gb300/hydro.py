@@ -45,7 +45,7 @@ EXPORTS = (
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
     "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk", "hydro_set_tile",
     "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
-    "hydro_selftest_math", "hydro_selftest_device_once", "hydro_batch_workspace_bytes", "hydro_batch_init",
+    "hydro_selftest_math", "hydro_selftest_device_once", "hydro_fma_probe", "hydro_fma_probe_flops", "hydro_batch_workspace_bytes", "hydro_batch_init",
     "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
     "hydro_batch_create", "hydro_batch_add", "hydro_batch_remove", "hydro_batch_set_graph",
     "hydro_batch_configure", "hydro_batch_variant_shape", "hydro_batch_step", "hydro_batch_reduce",
@@ -122,6 +122,10 @@ def load(path: str = LIB_PATH):
     L.hydro_strerror.argtypes = [C.c_int]
     L.hydro_selftest_math.restype = C.c_int
     L.hydro_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_long, vp]
+    L.hydro_fma_probe.restype = C.c_int
+    L.hydro_fma_probe.argtypes = [C.c_int, C.c_longlong, C.c_int, C.c_int, vp, vp]
+    L.hydro_fma_probe_flops.restype = C.c_double
+    L.hydro_fma_probe_flops.argtypes = [C.c_longlong, C.c_int, C.c_int]
     L.hydro_selftest_device_once.restype = C.c_int
     L.hydro_selftest_device_once.argtypes = [C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     PP = C.POINTER(C.c_void_p)
@@ -338,6 +342,15 @@ def hydro_selftest_device_once(devs, fail_dev: int = -1, threads: int = 1, ndev:
                                              int(ndev), once.ctypes.data_as(ip), vcalls.ctypes.data_as(ip),
                                              vals.ctypes.data_as(ip)), "hydro_selftest_device_once")
     return once, vcalls, vals
+
+
+def hydro_fma_probe(precision: int, iters: int, ctas: int, threads: int, out: int, stream: int):
+    _check(load().hydro_fma_probe(int(precision), int(iters), int(ctas), int(threads), C.c_void_p(out),
+                                  C.c_void_p(stream)), "hydro_fma_probe")
+
+
+def hydro_fma_probe_flops(iters: int, ctas: int, threads: int) -> float:
+    return load().hydro_fma_probe_flops(int(iters), int(ctas), int(threads))
 
 
 def hydro_destroy(h):

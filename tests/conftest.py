@@ -11,6 +11,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running check")
+    config.addinivalue_line("markers", "headline: the full-size headline workload against the oracle "
+                                       "(minutes of host time)")
 
 
 @pytest.fixture(scope="session")
