@@ -88,6 +88,9 @@ CONFIGS = {
                         "reductions, 150 GB HBM budget, continuous batching"),
     "served-saturation": dict(served=True, rate=500.0,
                               desc="served workload as above with arrivals 10x faster (saturation run)"),
+    "served-light": dict(served=True, rate=10.0,
+                         desc="served workload as above with arrivals at 10/s (a load the GPU carries: "
+                              "latency without queueing)"),
     "rt256-fp64-rk2": dict(n=256, precision=inputs.FP64, hse=0, scheme=inputs.SSPRK2,
                            desc="3D Rayleigh-Taylor 256^3 FP64 with the SSP-RK2 method-of-lines integrator "
                                 "(two stage kernels per step)"),
@@ -539,7 +542,11 @@ def run_gpu_batch(args):
     c = CONFIGS[args.config]
     items = kh_batch_items(c["count"])
     b = hydro.Batch(items)
-    tune = autotune.tune_batch(b, use_cache=not args.retune)
+    if args.no_tune:
+        tune = {"variant": 7, "tile": [32, 16], "async_staging": True, "zchunk": 0, "cached": False,
+                "note": "library defaults (no autotuning)"}
+    else:
+        tune = autotune.tune_batch(b, use_cache=not args.retune)
     b.step(args.warmup)
     torch.cuda.synchronize()
     n0 = b.launches()
@@ -604,11 +611,32 @@ def run_served(args):
     # payloads are built ahead of admission on a background thread
     reqs = serve.requests_from_inputs(count=args.requests, rate=c["rate"], lazy=True)
     prep_s = time.perf_counter() - t0
+    # the three cheapest requests' results are kept for the FP32 error against the oracle
+    check_ids = {r.id for r in sorted(reqs, key=lambda r: r.n ** (2 if r.family == "kh2d" else 3) * r.steps)[:3]}
     srv = serve.Server(budget_bytes=args.budget_gb * 1e9, max_active=args.max_active)
     barrier(world)
     with ClockSampler(local) as clk:
-        stats = srv.run(reqs)
+        stats = srv.run(reqs, keep_results=lambda r: r.id in check_ids)
     srv.close()
+    accuracy = None
+    if rank == 0 and not args.no_accuracy:
+        import oracle
+
+        oracle.build()
+        worst, checked = 0.0, []
+        for r in reqs:
+            if r.id not in check_ids or r.result is None:
+                continue
+            p = serve.make_payload(serve.Request(id=r.id, arrival=0.0, family=r.family, n=r.n, steps=r.steps,
+                                                 seed=r.seed))
+            o = oracle.Oracle(p.prob.replace(precision=inputs.FP64))
+            V, _, _, _ = o.run(o.state_from_prim(p.W), max_steps=r.steps)
+            rho = o.total(V)[0]
+            rho_gpu = o.total(r.result.astype(np.float64))[0]
+            worst = max(worst, float(np.abs(rho_gpu - rho).sum() / np.abs(rho).sum()))
+            checked.append(f"{r.family} n={r.n} steps={r.steps}")
+        accuracy = {"vs": "FP64 CPU oracle, same steps from the same seeded state", "requests": checked,
+                    "density_l1_rel_max": worst}
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     busy_gbs = stats["busy_hbm_gbs"] or 0.0
@@ -623,7 +651,8 @@ def run_served(args):
                        "budget_gb": args.budget_gb, "max_active": args.max_active,
                        "request_stream_prep_s": prep_s,
                        "payloads": "initial fields built on a background thread ahead of admission (seeded)",
-                       "step": "one tick = one batched step of every active solve",
+                       "step": "one tick = one batched step of every active solve; steps, admissions and "
+                               "retirements enqueued without stream synchronisation, up to 8 steps in flight",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "latency": {"p50_s": stats["p50_latency_s"], "p99_s": stats["p99_latency_s"],
                         "makespan_s": stats["makespan_s"]},
@@ -632,6 +661,7 @@ def run_served(args):
                          "kernel": "step3d_batch_kernel<float> + step2d_batch_kernel<float>",
                          "note": "algorithmic bytes over busy (tick) time"},
             "busy_zone_updates_per_s": stats["busy_zone_updates_per_s"],
+            "accuracy": accuracy,
             "cpu_baseline": None, "e2e": None, "gpu_launches": stats["launches"], "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -160,7 +160,11 @@ int hydro_advance_to(hydro_sim *sim, double t_end, long max_steps, long *nsteps_
 /* Reductions of the current state (see HYDRO_RED_*); synchronises. */
 int hydro_reduce(hydro_sim *sim, int what, double *out);
 
-/* Device pointer of the buffer that holds the current state. */
+/* Device pointer of the buffer that holds the current state.  Launches
+   made after time reached a target (hydro_advance_to) or after an error
+   move nothing, so the current buffer follows the device's step count; it
+   is exact after any call that synchronises (hydro_advance_to,
+   hydro_reduce, hydro_step with dt_taken, the state and field calls). */
 void *hydro_current(hydro_sim *sim);
 
 /* Raw stored state (hydro_state_bytes) to / from HOST memory, for
@@ -243,19 +247,25 @@ const char *hydro_strerror(int status);
 /* ---------------------------------------------------------------------
    Batched solves.  Many independent instances of different sizes (2D and
    3D, one precision; one hydrostatic-background flag for the 3D ones) step
-   together: each step is one persistent launch over a device-resident work
-   list of (instance, tile, z-chunk) items for the 3D instances and one for
-   the 2D instances, replayed from a captured CUDA graph when the stream is
-   not the legacy default stream.  Each instance keeps its own time-control
-   block and CFL dt (the last item of an instance to finish sets it).
-   Instances may join (hydro_batch_add) and leave (hydro_batch_remove)
-   between steps; the work lists and graph are rebuilt on the next step.  The
-   paper motivates such suites as capacity computing for parameter studies
-   and uncertainty quantification ("Increasing computing power",
-   "Capabilities needed").  All buffers are caller-owned device memory,
-   256-byte aligned: per instance two state buffers (hydro_state_bytes) and
-   one instance work buffer (hydro_instance_work_bytes), plus one batch work
-   buffer (hydro_batch_create_bytes). */
+   together: each step is one persistent launch for the 3D instances and one
+   for the 2D instances, whose CTAs claim work items (instance, tile,
+   z-chunk) from a device-resident queue, largest first; the launches are
+   replayed from a captured CUDA graph when the stream is not the legacy
+   default stream.  Each instance keeps its own time-control block and CFL
+   dt (the last item of an instance to finish sets it) and its own step
+   limit, after which the kernels skip it.  Instances may join and leave
+   between steps: the queue, the instance table and the item lists live in
+   device memory and are rewritten by stream-ordered copies from pinned host
+   staging, so membership changes need no synchronisation and no new graph
+   (hydro_batch_add_async / hydro_batch_remove_async; the plain add and
+   remove synchronise).  The paper motivates such suites as capacity
+   computing for parameter studies and uncertainty quantification
+   ("Increasing computing power", "Capabilities needed").  All device
+   buffers are caller-owned, 256-byte aligned: per instance two state
+   buffers (hydro_state_bytes) and one instance work buffer
+   (hydro_instance_work_bytes), plus one batch work buffer
+   (hydro_batch_create_bytes).  The handle keeps a pinned host staging
+   buffer for the uploads. */
 typedef struct hydro_batch hydro_batch;
 
 /* Per-instance work buffer (time control, partial slots, background
@@ -278,8 +288,20 @@ int hydro_batch_create(int max_instances, long max_items3d, long max_items2d, in
    mode different from the batch's.  Synchronises. */
 int hydro_batch_add(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
                     const double *W0, const double *bg, long step_end, int *id);
+/* hydro_batch_add without synchronisation: W0_device is a DEVICE array of
+   the FP64 total primitives (nvar planes of N), which the conversion
+   kernel, enqueued on the batch stream, reads; it and the host tables bg
+   (copied before return) may be released once the work enqueued so far has
+   run (record an event on the stream).  Errors of the initial state surface
+   through the instance's control block (hydro_batch_reduce). */
+int hydro_batch_add_async(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
+                          const double *W0_device, const double *bg, long step_end, int *id);
 /* Remove an instance (synchronises; its buffers are free on return). */
 int hydro_batch_remove(hydro_batch *b, int id);
+/* Remove an instance without synchronisation: launches enqueued before the
+   call still use its buffers, so the caller releases them only after that
+   work has run (an event recorded on the stream after this call). */
+int hydro_batch_remove_async(hydro_batch *b, int id);
 /* Graph capture on (default) or off (direct launches). */
 int hydro_batch_set_graph(hydro_batch *b, int on);
 
@@ -291,10 +313,12 @@ int hydro_batch_init(const hydro_problem *probs, int count, void *const *Ua, voi
                      hydro_batch **out);
 
 /* Select the 3D tile shape and staging depth (variant index, see
-   hydro_set_tile; variants 3 and 7 are FP32 only) and the z-chunk length
-   (0 = default); rebuilds the work lists and the graph.  Results do not
-   depend on this choice.  hydro_batch_variant_shape gives a variant's tile
-   shape (tx x ty); variants v and v + 4 share it. */
+   hydro_set_tile; variants 3 and 7 are FP32 only) and the longest z-chunk
+   of an instance's column (0 = default, 64 planes; each column is cut into
+   chunks of nearly equal length); rebuilds the work lists (and the graph
+   when the kernel changes).  Results do not depend on this choice.
+   hydro_batch_variant_shape gives a variant's tile shape (tx x ty);
+   variants v and v + 4 share it. */
 int hydro_batch_configure(hydro_batch *b, int variant, int zchunk);
 int hydro_batch_variant_shape(int variant, int *tx, int *ty);
 
@@ -306,9 +330,14 @@ int hydro_batch_step(hydro_batch *b, long nsteps);
 int hydro_batch_reduce(hydro_batch *b, int id, int what, double *out);
 int hydro_batch_get_fields(hydro_batch *b, int id, int what, double *host_dst);
 /* Raw stored state of an instance to HOST memory (synchronises); device
-   pointer of the buffer holding it. */
+   pointer of the buffer holding it (synchronises). */
 int hydro_batch_get_state(hydro_batch *b, int id, void *host_dst);
 void *hydro_batch_current(hydro_batch *b, int id);
+/* Enqueue the copy of an instance's state, as it will be once the launches
+   enqueued so far have run, to host_dst (pinned host memory for a truly
+   asynchronous copy); no synchronisation.  Meaningful for an instance that
+   did not enter its error state. */
+int hydro_batch_get_state_async(hydro_batch *b, int id, void *host_dst);
 
 /* Kernel launches so far; work-list sizes and persistent grid sizes. */
 long hydro_batch_launch_count(hydro_batch *b);

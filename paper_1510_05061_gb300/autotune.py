@@ -20,7 +20,8 @@ from typing import Dict, Iterable, Optional
 
 from . import inputs
 
-DEFAULT_ZCHUNKS = (8, 16, 32, 64)
+# longest z-chunk of an instance's column in a batch (shorter columns are one item)
+DEFAULT_ZCHUNKS = (16, 32, 64, 128, 256)
 
 
 def cache_path() -> str:
@@ -39,7 +40,7 @@ def signature(batch) -> str:
     hse = int(any(p.hse_subtract for p in p3))
     mag = f"{cells:.2g}" if cells else "0"
     span = f"{ns[0]}-{ns[-1]}" if ns else "none"
-    return f"{torch.cuda.get_device_name()}|{prec}|hse{hse}|n3d={len(p3)}|cells={mag}|n={span}"
+    return f"{torch.cuda.get_device_name()}|batch-v2|{prec}|hse{hse}|n3d={len(p3)}|cells={mag}|n={span}"
 
 
 def _load_cache() -> Dict[str, dict]:

@@ -24,8 +24,8 @@ struct Batch2D {
 
 }  // namespace
 
-cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, const BatchItem *items, int nitems,
-                           int parity, int grid, cudaStream_t s)
+cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, BatchQueue *q, int parity, int grid,
+                           cudaStream_t s)
 {
     constexpr int NT = BATCH2D_TX * BATCH2D_TY;
     if (fp32) {
@@ -33,13 +33,13 @@ cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, const BatchItem *i
         cudaError_t e = Batch2D<float>::ensure(&cap);
         if (e != cudaSuccess) return e;
         step2d_batch_kernel<float, BATCH2D_TX, BATCH2D_TY>
-            <<<grid, NT, Step2DSmem<float, BATCH2D_TX, BATCH2D_TY>::bytes, s>>>(insts, items, nitems, parity);
+            <<<grid, NT, Step2DSmem<float, BATCH2D_TX, BATCH2D_TY>::bytes, s>>>(insts, q, parity);
     } else {
         int cap = 0;
         cudaError_t e = Batch2D<double>::ensure(&cap);
         if (e != cudaSuccess) return e;
         step2d_batch_kernel<double, BATCH2D_TX, BATCH2D_TY>
-            <<<grid, NT, Step2DSmem<double, BATCH2D_TX, BATCH2D_TY>::bytes, s>>>(insts, items, nitems, parity);
+            <<<grid, NT, Step2DSmem<double, BATCH2D_TX, BATCH2D_TY>::bytes, s>>>(insts, q, parity);
     }
     return cudaGetLastError();
 }

@@ -16,14 +16,13 @@ struct Batch3D {
         return persistent_grid(cache, step3d_batch_kernel<T, HSE, TX, TY, AS>,
                                Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes, TX * TY, grid);
     }
-    static cudaError_t launch(const BatchInst *insts, const BatchItem *items, int nitems, int parity,
-                              int grid, cudaStream_t s)
+    static cudaError_t launch(const BatchInst *insts, BatchQueue *q, int parity, int grid, cudaStream_t s)
     {
         int cap = 0;
         cudaError_t e = ensure(&cap);
         if (e != cudaSuccess) return e;
         step3d_batch_kernel<T, HSE, TX, TY, AS>
-            <<<grid, TX * TY, Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes, s>>>(insts, items, nitems, parity);
+            <<<grid, TX * TY, Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes, s>>>(insts, q, parity);
         return cudaGetLastError();
     }
     static int max_grid()
@@ -34,16 +33,15 @@ struct Batch3D {
 };
 
 template <bool HSE>
-cudaError_t launch_v(int v, const BatchInst *insts, const BatchItem *items, int nitems, int parity,
-                     int grid, cudaStream_t s)
+cudaError_t launch_v(int v, const BatchInst *insts, BatchQueue *q, int parity, int grid, cudaStream_t s)
 {
     switch (v) {
-    case 0: return Batch3D<double, HSE, 32, 8, false>::launch(insts, items, nitems, parity, grid, s);
-    case 1: return Batch3D<double, HSE, 32, 4, false>::launch(insts, items, nitems, parity, grid, s);
-    case 2: return Batch3D<double, HSE, 16, 16, false>::launch(insts, items, nitems, parity, grid, s);
-    case 4: return Batch3D<double, HSE, 32, 8, true>::launch(insts, items, nitems, parity, grid, s);
-    case 5: return Batch3D<double, HSE, 32, 4, true>::launch(insts, items, nitems, parity, grid, s);
-    case 6: return Batch3D<double, HSE, 16, 16, true>::launch(insts, items, nitems, parity, grid, s);
+    case 0: return Batch3D<double, HSE, 32, 8, false>::launch(insts, q, parity, grid, s);
+    case 1: return Batch3D<double, HSE, 32, 4, false>::launch(insts, q, parity, grid, s);
+    case 2: return Batch3D<double, HSE, 16, 16, false>::launch(insts, q, parity, grid, s);
+    case 4: return Batch3D<double, HSE, 32, 8, true>::launch(insts, q, parity, grid, s);
+    case 5: return Batch3D<double, HSE, 32, 4, true>::launch(insts, q, parity, grid, s);
+    case 6: return Batch3D<double, HSE, 16, 16, true>::launch(insts, q, parity, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -64,11 +62,10 @@ int grid_v(int v)
 
 }  // namespace
 
-cudaError_t launch_batch3d_f64(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
-                               int nitems, int parity, int grid, cudaStream_t s)
+cudaError_t launch_batch3d_f64(int variant, bool hse, const BatchInst *insts, BatchQueue *q, int parity,
+                               int grid, cudaStream_t s)
 {
-    return hse ? launch_v<true>(variant, insts, items, nitems, parity, grid, s)
-               : launch_v<false>(variant, insts, items, nitems, parity, grid, s);
+    return hse ? launch_v<true>(variant, insts, q, parity, grid, s) : launch_v<false>(variant, insts, q, parity, grid, s);
 }
 
 int batch3d_max_grid_f64(int variant, bool hse)

@@ -1,16 +1,20 @@
 // batch_api.cu -- batched solves: many independent, uneven instances
-// advanced together, one persistent launch per step over a device work list
-// (one launch for the 3D instances, one for the 2D ones), replayed from a
-// captured CUDA graph.  Instances may join and leave between steps (the
-// continuous-batching server uses that); the work lists and the graph are
-// rebuilt lazily when membership or configuration changes.
+// advanced together, one persistent launch per step (one for the 3D
+// instances, one for the 2D ones) whose CTAs claim work items from a
+// device-resident queue, replayed from a captured CUDA graph.  Instances may
+// join and leave between steps (the continuous-batching server does so
+// without synchronising: the queue, the instance table and the item lists
+// are rewritten by stream-ordered copies from pinned host memory, and the
+// graph, whose launches read them at run time, stays valid).
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -65,15 +69,17 @@ InstLayout inst_layout(const hydro_problem &p)
     return L;
 }
 
-// Shared work buffer: instance table and the two item lists.
+// Shared work buffer: the queue, the instance table and the two item lists.
 struct BatchLayout {
-    size_t insts, items3, items2, total;
+    size_t queue, insts, items3, items2, total;
 };
 
 BatchLayout batch_layout(int max_instances, long long cap3, long long cap2)
 {
     BatchLayout L{};
     size_t off = 0;
+    L.queue = off;
+    off = align_up(off + sizeof(BatchQueue));
     L.insts = off;
     off = align_up(off + sizeof(BatchInst) * (size_t)max_instances);
     L.items3 = off;
@@ -98,7 +104,14 @@ struct InstInfo {
     double dx[3], inv_dx[3], cell_volume;
     long long step_end;
     size_t items;           // max_items_of(prob)
+    int join_parity;        // batch parity of the first launch after the join: buf[join_parity] held U^0
+    long long launched;     // batched steps launched since the join
 };
+
+// Buffer index (into InstInfo::buf) of the state after `steps` steps: a
+// frozen instance (step limit reached, or its error state) is skipped by the
+// kernels, so its state stays in the buffer of its last step.
+int state_index(const InstInfo &I, long long steps) { return (int)((I.join_parity + (steps & 1)) & 1); }
 
 AuxArgs aux_for(const InstInfo &I, void *U)
 {
@@ -130,20 +143,25 @@ struct hydro_batch {
     unsigned char *work;
     BatchLayout lay;
     cudaStream_t stream;
-    int parity;                // buffer index holding every instance's current state
-    int variant, zchunk;       // zchunk 0 = default
-    bool dirty;                // work lists / graph need a rebuild
+    int parity;                // parity of the next launch
+    int variant, zchunk;       // zchunk: longest chunk of an instance's column (0 = default)
+    bool dirty;                // queue / tables need an upload
     bool use_graph;
-    std::vector<BatchInst> host_insts;
-    std::vector<BatchItem> host_items3, host_items2;
+    BatchQueue *d_queue;
     BatchInst *d_insts;
     BatchItem *d_items3, *d_items2;
+    // pinned host staging of the uploads; rewritten only after the previous
+    // upload from it has completed (event `staged`)
+    unsigned char *pinned;
+    size_t pinned_bytes;
+    cudaEvent_t staged;
+    bool staged_pending;
     int nitems3, nitems2, grid3, grid2;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     bool graph_ok;
+    int graph_variant, graph_has3, graph_has2;
     long launches;
-    std::vector<void *> owned_inst_work;   // convenience init: instance buffers inside `work`
 };
 
 namespace {
@@ -161,34 +179,55 @@ cudaError_t launch_once(hydro_batch *b, int parity)
 {
     cudaError_t e = cudaSuccess;
     if (b->nitems3 > 0)
-        e = launch_batch3d(b->variant, b->precision == HYDRO_FP32, b->hse3 == 1, b->d_insts, b->d_items3,
-                           b->nitems3, parity, b->grid3, b->stream);
+        e = launch_batch3d(b->variant, b->precision == HYDRO_FP32, b->hse3 == 1, b->d_insts, b->d_queue, parity,
+                           b->grid3, b->stream);
     if (e == cudaSuccess && b->nitems2 > 0)
-        e = launch_batch2d(b->precision == HYDRO_FP32, b->d_insts, b->d_items2, b->nitems2, parity,
-                           b->grid2, b->stream);
+        e = launch_batch2d(b->precision == HYDRO_FP32, b->d_insts, b->d_queue, parity, b->grid2, b->stream);
     return e;
 }
 
-int effective_zchunk(const hydro_batch *b)
+// Longest z-chunk of an instance's column: long chunks re-read few halo
+// planes (4 per chunk), and the largest-first claim order keeps the SMs
+// balanced even when whole columns are single items.
+constexpr int BATCH_ZCHUNK_DEFAULT = 64;
+
+int zchunk_of(const hydro_batch *b, const hydro_problem &p)
 {
-    if (b->zchunk > 0) return b->zchunk;
-    // a few planes per item keeps the item count high enough for balance
-    // across the SMs and the chunk-end overhead (two extra planes) small
-    long long cells = 0;
-    for (const InstInfo &I : b->inst)
-        if (I.active && I.prob.ndim == 3) cells += I.N;
-    return cells > (1ll << 24) ? 16 : 8;
+    const int zmax = b->zchunk > 0 ? b->zchunk : BATCH_ZCHUNK_DEFAULT;
+    const int nch = (p.n[2] + zmax - 1) / zmax;       // chunks of (nearly) equal length
+    return (p.n[2] + nch - 1) / nch;
 }
 
-// Rebuild the work lists and per-instance arguments, upload them and
-// capture the two-launch (both parities) graph.
+int ensure_pinned(hydro_batch *b, size_t need)
+{
+    if (need <= b->pinned_bytes) return HYDRO_OK;
+    if (b->staged_pending && cudaEventSynchronize(b->staged) != cudaSuccess) return HYDRO_ERR_CUDA;
+    b->staged_pending = false;
+    if (b->pinned) cudaFreeHost(b->pinned);
+    b->pinned = nullptr;
+    b->pinned_bytes = 0;
+    size_t cap = 1 << 20;
+    while (cap < need) cap *= 2;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&b->pinned), cap, cudaHostAllocDefault) != cudaSuccess) {
+        b->pinned = nullptr;
+        return HYDRO_ERR_OOM;
+    }
+    b->pinned_bytes = cap;
+    return HYDRO_OK;
+}
+
+// Rebuild the per-instance arguments and the item lists and upload them
+// (with the queue's list lengths) by stream-ordered copies: launches already
+// enqueued still see the old ones, later launches the new ones.  Items are
+// ordered largest first (3D: by chunk length) for the dynamic claim.  The
+// graph (two launches, both parities) is captured again only when the
+// kernels or grids change, not when the membership does.
 int rebuild(hydro_batch *b)
 {
     const TileShape ts = TILE3D_SHAPES[b->variant];
-    const int zdef = effective_zchunk(b);
-    b->host_insts.assign(b->max_instances, BatchInst{});
-    b->host_items3.clear();
-    b->host_items2.clear();
+    std::vector<BatchInst> insts(b->max_instances, BatchInst{});
+    std::vector<BatchItem> items3, items2;
+    std::vector<int> len3;
     for (int i = 0; i < (int)b->inst.size(); ++i) {
         const InstInfo &I = b->inst[i];
         if (!I.active) continue;
@@ -196,9 +235,9 @@ int rebuild(hydro_batch *b)
         const bool is3 = p.ndim == 3;
         const int tx = is3 ? ts.tx : BATCH2D_TX, ty = is3 ? ts.ty : BATCH2D_TY;
         const int tiles_x = tiles_along(p.n[0], tx), tiles_y = tiles_along(p.n[1], ty);
-        const int zc = is3 ? std::min(zdef, p.n[2]) : 1;
+        const int zc = is3 ? zchunk_of(b, p) : 1;
         const int nch = is3 ? (p.n[2] + zc - 1) / zc : 1;
-        BatchInst &bi = b->host_insts[i];
+        BatchInst &bi = insts[i];
         bi.nitems = tiles_x * tiles_y * nch;
         for (int par = 0; par < 2; ++par) {
             StepArgs &a = bi.a[par];
@@ -228,55 +267,94 @@ int rebuild(hydro_batch *b)
             a.tiles_x = tiles_x;
             fill_fp32_constants(a);
         }
-        std::vector<BatchItem> &lst = is3 ? b->host_items3 : b->host_items2;
         int local = 0;
         for (int c = 0; c < nch; ++c)
-            for (int t = 0; t < tiles_x * tiles_y; ++t) lst.push_back(BatchItem{i, t, c, local++});
+            for (int t = 0; t < tiles_x * tiles_y; ++t) {
+                if (is3) {
+                    items3.push_back(BatchItem{i, t, c, local++});
+                    len3.push_back(std::min(zc, p.n[2] - c * zc));
+                } else {
+                    items2.push_back(BatchItem{i, t, c, local++});
+                }
+            }
     }
-    if ((long long)b->host_items3.size() > b->cap3 || (long long)b->host_items2.size() > b->cap2)
-        return HYDRO_ERR_OOM;
-    b->nitems3 = (int)b->host_items3.size();
-    b->nitems2 = (int)b->host_items2.size();
-    cudaError_t e = cudaMemcpyAsync(b->d_insts, b->host_insts.data(), sizeof(BatchInst) * b->max_instances,
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && b->nitems3)
-        e = cudaMemcpyAsync(b->d_items3, b->host_items3.data(), sizeof(BatchItem) * b->nitems3,
-                            cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && b->nitems2)
-        e = cudaMemcpyAsync(b->d_items2, b->host_items2.data(), sizeof(BatchItem) * b->nitems2,
-                            cudaMemcpyHostToDevice, b->stream);
-    // the host vectors are staging for these copies; they may change on the
-    // next rebuild only after the copies are done
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
-    const bool fp32 = b->precision == HYDRO_FP32;
-    b->grid3 = b->nitems3 ? std::max(1, std::min(b->nitems3, batch3d_max_grid(b->variant, fp32, b->hse3 == 1))) : 0;
-    b->grid2 = b->nitems2 ? std::max(1, std::min(b->nitems2, batch2d_max_grid(fp32))) : 0;
+    if ((long long)items3.size() > b->cap3 || (long long)items2.size() > b->cap2) return HYDRO_ERR_OOM;
+    // largest first (stable: an instance's items stay in tile order)
+    std::vector<int> order(items3.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return len3[x] > len3[y]; });
+    std::vector<BatchItem> sorted3(items3.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted3[k] = items3[order[k]];
 
-    drop_graph(b);
-    if (b->use_graph && b->stream != nullptr && (b->nitems3 || b->nitems2)) {
-        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t e0 = launch_once(b, 0);
-            cudaError_t e1 = e0 == cudaSuccess ? launch_once(b, 1) : e0;
-            e = cudaStreamEndCapture(b->stream, &b->graph);
-            if (e == cudaSuccess && e1 == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-            else if (e == cudaSuccess) e = e1;
-            b->graph_ok = e == cudaSuccess;
-        }
-        if (!b->graph_ok) {
-            drop_graph(b);
-            cudaGetLastError();   // capture failures are not sticky: launch directly instead
+    b->nitems3 = (int)sorted3.size();
+    b->nitems2 = (int)items2.size();
+    const size_t bi_bytes = sizeof(BatchInst) * (size_t)b->max_instances;
+    const size_t i3_bytes = sizeof(BatchItem) * sorted3.size();
+    const size_t i2_bytes = sizeof(BatchItem) * items2.size();
+    const size_t q_bytes = offsetof(BatchQueue, next);   // list pointers and lengths, not the counters
+    const size_t o_i3 = align_up(bi_bytes), o_i2 = o_i3 + align_up(i3_bytes), o_q = o_i2 + align_up(i2_bytes);
+    int rc = ensure_pinned(b, o_q + align_up(q_bytes));
+    if (rc) return rc;
+    if (b->staged_pending && cudaEventSynchronize(b->staged) != cudaSuccess) return HYDRO_ERR_CUDA;
+    std::memcpy(b->pinned, insts.data(), bi_bytes);
+    if (i3_bytes) std::memcpy(b->pinned + o_i3, sorted3.data(), i3_bytes);
+    if (i2_bytes) std::memcpy(b->pinned + o_i2, items2.data(), i2_bytes);
+    BatchQueue qh{};
+    qh.items[0] = b->d_items3;
+    qh.items[1] = b->d_items2;
+    qh.nitems[0] = b->nitems3;
+    qh.nitems[1] = b->nitems2;
+    std::memcpy(b->pinned + o_q, &qh, q_bytes);
+    cudaError_t e = cudaMemcpyAsync(b->d_insts, b->pinned, bi_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && i3_bytes)
+        e = cudaMemcpyAsync(b->d_items3, b->pinned + o_i3, i3_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && i2_bytes)
+        e = cudaMemcpyAsync(b->d_items2, b->pinned + o_i2, i2_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_queue, b->pinned + o_q, q_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    b->staged_pending = true;
+
+    // persistent grids: the resident CTAs (the claim loop balances the items)
+    const bool fp32 = b->precision == HYDRO_FP32;
+    b->grid3 = b->nitems3 ? std::max(1, batch3d_max_grid(b->variant, fp32, b->hse3 == 1)) : 0;
+    b->grid2 = b->nitems2 ? std::max(1, batch2d_max_grid(fp32)) : 0;
+
+    const bool has3 = b->nitems3 > 0, has2 = b->nitems2 > 0;
+    const bool same_graph = b->graph_ok && b->graph_variant == b->variant && b->graph_has3 == has3 &&
+                            b->graph_has2 == has2;
+    if (!same_graph) {
+        drop_graph(b);
+        if (b->use_graph && b->stream != nullptr && (has3 || has2)) {
+            e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e0 = launch_once(b, 0);
+                cudaError_t e1 = e0 == cudaSuccess ? launch_once(b, 1) : e0;
+                e = cudaStreamEndCapture(b->stream, &b->graph);
+                if (e == cudaSuccess && e1 == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+                else if (e == cudaSuccess) e = e1;
+                b->graph_ok = e == cudaSuccess;
+            }
+            if (!b->graph_ok) {
+                drop_graph(b);
+                cudaGetLastError();   // capture failures are not sticky: launch directly instead
+            }
+            b->graph_variant = b->variant;
+            b->graph_has3 = has3;
+            b->graph_has2 = has2;
         }
     }
     b->dirty = false;
     return HYDRO_OK;
 }
 
-int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
-                 const double *W0, const double *bg, long long step_end, int *id_out)
+// Checks and bookkeeping shared by the synchronous and asynchronous adds;
+// fills *I (buffers, layout, background tables uploaded on the stream) and
+// the slot.  The initial state is converted by the caller.
+int prepare_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
+                     const double *bg, long long step_end, InstInfo *Iout, int *slot_out)
 {
-    if (!prob || !Ua || !Ub || !inst_work || !W0 || Ua == Ub) return HYDRO_ERR_INVALID_ARG;
+    if (!prob || !Ua || !Ub || !inst_work || Ua == Ub) return HYDRO_ERR_INVALID_ARG;
     if (!aligned(Ua) || !aligned(Ub) || !aligned(inst_work)) return HYDRO_ERR_INVALID_ARG;
     if (hydro_state_bytes(prob) == 0 || prob->precision != b->precision) return HYDRO_ERR_INVALID_ARG;
     if (prob->scheme != HYDRO_SCHEME_HANCOCK) return HYDRO_ERR_INVALID_ARG;   // batches step MUSCL-Hancock
@@ -290,11 +368,7 @@ int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, 
     int slot = -1;
     for (int i = 0; i < (int)b->inst.size(); ++i)
         if (!b->inst[i].active) { slot = i; break; }
-    if (slot < 0) {
-        if ((int)b->inst.size() >= b->max_instances) return HYDRO_ERR_OOM;
-        b->inst.push_back(InstInfo{});
-        slot = (int)b->inst.size() - 1;
-    }
+    if (slot < 0 && (int)b->inst.size() >= b->max_instances) return HYDRO_ERR_OOM;
     // the new instance's items must fit the work lists together with the others
     long long need3 = 0, need2 = 0;
     for (const InstInfo &J : b->inst)
@@ -308,7 +382,10 @@ int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, 
     I.plane = (long long)prob->n[0] * prob->n[1];
     I.N = I.plane * prob->n[2];
     I.state_bytes = hydro_state_bytes(prob);
-    // the instance joins at the batch's current parity
+    // the instance joins at the batch's current parity: the next launch
+    // (parity b->parity) reads buf[b->parity] = Ua
+    I.join_parity = b->parity;
+    I.launched = 0;
     I.buf[b->parity] = Ua;
     I.buf[1 - b->parity] = Ub;
     const InstLayout L = inst_layout(*prob);
@@ -326,13 +403,11 @@ int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, 
         if (d < prob->ndim) I.cell_volume *= I.dx[d];
     }
     cudaError_t e = cudaMemsetAsync(inst_work, 0, L.total, b->stream);
-    std::vector<PlaneBG> tb;
-    std::vector<PlaneBGT<float>> tf;
     if (e == cudaSuccess && prob->hse_subtract) {
         const int nz = prob->n[2];
         const double *rc_ = bg, *pc_ = bg + (nz + 4), *rf_ = bg + 2 * (nz + 4), *pf_ = bg + 2 * (nz + 4) + (nz + 5);
-        tb.assign(nz + 5, PlaneBG{});
-        tf.assign(nz + 5, PlaneBGT<float>{});
+        std::vector<PlaneBG> tb(nz + 5, PlaneBG{});
+        std::vector<PlaneBGT<float>> tf(nz + 5, PlaneBGT<float>{});
         for (int k = -2; k <= nz + 2; ++k) {
             PlaneBG &q = tb[k + 2];
             const bool has_c = k <= nz + 1;
@@ -350,15 +425,45 @@ int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, 
             tf[k + 2] = PlaneBGT<float>{(float)q.rho_c, (float)q.p_c, (float)q.rho_f, (float)q.p_f,
                                         (float)q.drho, (float)q.dp, (float)q.B, 0.0f};
         }
+        // (copies from pageable memory have read the vectors when they return)
         e = cudaMemcpyAsync(I.bg, tb.data(), sizeof(PlaneBG) * tb.size(), cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(I.bgf, tf.data(), sizeof(PlaneBGT<float>) * tf.size(), cudaMemcpyHostToDevice,
                                 b->stream);
     }
-    // initial state through the spare buffer, then the first dt
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    *Iout = I;
+    *slot_out = slot;
+    return HYDRO_OK;
+}
+
+void commit_instance(hydro_batch *b, const InstInfo &I, int slot, int *id_out)
+{
+    if (slot < 0) {
+        b->inst.push_back(InstInfo{});
+        slot = (int)b->inst.size() - 1;
+    }
+    b->inst[slot] = I;
+    b->inst[slot].active = true;
+    if (I.prob.ndim == 3) b->hse3 = I.prob.hse_subtract;
+    b->dirty = true;
+    *id_out = slot;
+}
+
+// Synchronous add: the host primitives go through the spare buffer in
+// chunks; the first dt is read back.
+int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
+                 const double *W0, const double *bg, long long step_end, int *id_out)
+{
+    if (!W0) return HYDRO_ERR_INVALID_ARG;
+    InstInfo I{};
+    int slot = -1;
+    int rc = prepare_instance(b, prob, Ua, Ub, inst_work, bg, step_end, &I, &slot);
+    if (rc) return rc;
     const long long cap = (long long)(I.state_bytes / (sizeof(double) * I.nvar));
     double *stg = static_cast<double *>(I.buf[1 - b->parity]);
     AuxArgs a = aux_for(I, I.buf[b->parity]);
+    cudaError_t e = cudaSuccess;
     for (long long c0 = 0; c0 < I.N && e == cudaSuccess; c0 += cap) {
         const long long m = std::min(cap, I.N - c0);
         for (int q = 0; q < I.nvar && e == cudaSuccess; ++q)
@@ -373,17 +478,40 @@ int add_instance(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
     b->launches += 2;
-    I.active = true;
-    b->inst[slot] = I;
-    if (prob->ndim == 3) b->hse3 = prob->hse_subtract;
-    b->dirty = true;
-    *id_out = slot;
+    commit_instance(b, I, slot, id_out);
     return c.err ? HYDRO_ERR_NONPHYSICAL : HYDRO_OK;
+}
+
+// Asynchronous add: W0dev is a DEVICE array of the FP64 total primitives;
+// the conversion and the first dt are enqueued on the batch stream.
+int add_instance_async(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
+                       const double *W0dev, const double *bg, long long step_end, int *id_out)
+{
+    if (!W0dev) return HYDRO_ERR_INVALID_ARG;
+    InstInfo I{};
+    int slot = -1;
+    int rc = prepare_instance(b, prob, Ua, Ub, inst_work, bg, step_end, &I, &slot);
+    if (rc) return rc;
+    AuxArgs a = aux_for(I, I.buf[b->parity]);
+    cudaError_t e = launch_init_convert(a, W0dev, 0, I.N, b->stream);
+    if (e == cudaSuccess) e = launch_signal(a, b->stream);
+    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
+    b->launches += 2;
+    commit_instance(b, I, slot, id_out);
+    return HYDRO_OK;
 }
 
 bool valid_id(const hydro_batch *b, int id)
 {
     return b && id >= 0 && id < (int)b->inst.size() && b->inst[id].active;
+}
+
+// Control block of an instance (synchronises) and the buffer of its current state.
+int read_inst_ctrl(hydro_batch *b, const InstInfo &I, Ctrl *c)
+{
+    cudaError_t e = cudaMemcpyAsync(c, I.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_CUDA;
 }
 
 }  // namespace
@@ -427,11 +555,20 @@ int hydro_batch_create(int max_instances, long max_items3d, long max_items2d, in
     b->work = static_cast<unsigned char *>(work);
     b->lay = batch_layout(max_instances, max_items3d, max_items2d);
     b->stream = static_cast<cudaStream_t>(stream);
+    b->d_queue = reinterpret_cast<BatchQueue *>(b->work + b->lay.queue);
     b->d_insts = reinterpret_cast<BatchInst *>(b->work + b->lay.insts);
     b->d_items3 = reinterpret_cast<BatchItem *>(b->work + b->lay.items3);
     b->d_items2 = reinterpret_cast<BatchItem *>(b->work + b->lay.items2);
     b->use_graph = true;
     b->dirty = true;
+    b->graph_variant = -1;
+    // the queue's claim counters start at zero (the kernels reset them after each launch)
+    cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), b->stream);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete b;
+        return HYDRO_ERR_CUDA;
+    }
     *out = b;
     return HYDRO_OK;
 }
@@ -441,6 +578,13 @@ int hydro_batch_add(hydro_batch *b, const hydro_problem *prob, void *Ua, void *U
 {
     if (!b || !id) return HYDRO_ERR_INVALID_ARG;
     return add_instance(b, prob, Ua, Ub, inst_work, W0, bg, step_end, id);
+}
+
+int hydro_batch_add_async(hydro_batch *b, const hydro_problem *prob, void *Ua, void *Ub, void *inst_work,
+                          const double *W0_device, const double *bg, long step_end, int *id)
+{
+    if (!b || !id) return HYDRO_ERR_INVALID_ARG;
+    return add_instance_async(b, prob, Ua, Ub, inst_work, W0_device, bg, step_end, id);
 }
 
 int hydro_batch_remove(hydro_batch *b, int id)
@@ -453,10 +597,20 @@ int hydro_batch_remove(hydro_batch *b, int id)
     return HYDRO_OK;
 }
 
+int hydro_batch_remove_async(hydro_batch *b, int id)
+{
+    if (!valid_id(b, id)) return HYDRO_ERR_INVALID_ARG;
+    b->inst[id].active = false;
+    b->dirty = true;
+    return HYDRO_OK;
+}
+
 int hydro_batch_set_graph(hydro_batch *b, int on)
 {
     if (!b) return HYDRO_ERR_INVALID_ARG;
     b->use_graph = on != 0;
+    drop_graph(b);
+    b->graph_variant = -1;
     b->dirty = true;
     return HYDRO_OK;
 }
@@ -498,8 +652,7 @@ int hydro_batch_init(const hydro_problem *probs, int count, void *const *Ua, voi
     }
     if (rc == HYDRO_OK) rc = rebuild(b);
     if (rc) {
-        drop_graph(b);
-        delete b;
+        hydro_batch_destroy(b);
         return rc;
     }
     *out = b;
@@ -509,7 +662,6 @@ int hydro_batch_init(const hydro_problem *probs, int count, void *const *Ua, voi
 int hydro_batch_configure(hydro_batch *b, int variant, int zchunk)
 {
     if (!b || !tile3d_available(variant, b->precision == HYDRO_FP32) || zchunk < 0) return HYDRO_ERR_INVALID_ARG;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
     b->variant = variant;
     b->zchunk = zchunk;
     return rebuild(b);
@@ -549,6 +701,8 @@ int hydro_batch_step(hydro_batch *b, long nsteps)
             b->launches += per;
         }
     }
+    for (InstInfo &I : b->inst)
+        if (I.active) I.launched += done;
     return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_CUDA;
 }
 
@@ -556,17 +710,17 @@ int hydro_batch_reduce(hydro_batch *b, int id, int what, double *out)
 {
     if (!valid_id(b, id) || !out) return HYDRO_ERR_INVALID_ARG;
     InstInfo &I = b->inst[id];
+    if (what < HYDRO_RED_TOTALS || what > HYDRO_RED_DT_LAST) return HYDRO_ERR_INVALID_ARG;
+    Ctrl c;
+    int rc = read_inst_ctrl(b, I, &c);
+    if (rc) return rc;
     if (what == HYDRO_RED_TOTALS) {
-        AuxArgs a = aux_for(I, I.buf[b->parity]);
+        AuxArgs a = aux_for(I, I.buf[state_index(I, c.step)]);
         b->launches += 1;
         if (launch_totals(a, b->stream) != cudaSuccess) return HYDRO_ERR_CUDA;
-    } else if (what < HYDRO_RED_DT || what > HYDRO_RED_DT_LAST) {
-        return HYDRO_ERR_INVALID_ARG;
+        rc = read_inst_ctrl(b, I, &c);
+        if (rc) return rc;
     }
-    Ctrl c;
-    cudaError_t e = cudaMemcpyAsync(&c, I.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return HYDRO_ERR_CUDA;
     switch (what) {
     case HYDRO_RED_TOTALS: for (int q = 0; q < I.nvar; ++q) out[q] = c.totals[q]; break;
     case HYDRO_RED_DT: out[0] = c.dt_next; break;
@@ -582,9 +736,13 @@ int hydro_batch_get_fields(hydro_batch *b, int id, int what, double *host_dst)
 {
     if (!valid_id(b, id) || !host_dst || (what != 0 && what != 1)) return HYDRO_ERR_INVALID_ARG;
     InstInfo &I = b->inst[id];
+    Ctrl c;
+    int rc = read_inst_ctrl(b, I, &c);
+    if (rc) return rc;
+    const int cur = state_index(I, c.step);
     const long long cap = (long long)(I.state_bytes / (sizeof(double) * I.nvar));
-    double *stg = static_cast<double *>(I.buf[1 - b->parity]);
-    AuxArgs a = aux_for(I, I.buf[b->parity]);
+    double *stg = static_cast<double *>(I.buf[1 - cur]);
+    AuxArgs a = aux_for(I, I.buf[cur]);
     for (long long c0 = 0; c0 < I.N; c0 += cap) {
         const long long m = std::min(cap, I.N - c0);
         b->launches += 1;
@@ -602,15 +760,34 @@ int hydro_batch_get_state(hydro_batch *b, int id, void *host_dst)
 {
     if (!valid_id(b, id) || !host_dst) return HYDRO_ERR_INVALID_ARG;
     InstInfo &I = b->inst[id];
-    cudaError_t e = cudaMemcpyAsync(host_dst, I.buf[b->parity], I.state_bytes, cudaMemcpyDeviceToHost, b->stream);
+    Ctrl c;
+    int rc = read_inst_ctrl(b, I, &c);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(host_dst, I.buf[state_index(I, c.step)], I.state_bytes, cudaMemcpyDeviceToHost,
+                                    b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_CUDA;
+}
+
+int hydro_batch_get_state_async(hydro_batch *b, int id, void *host_dst)
+{
+    if (!valid_id(b, id) || !host_dst) return HYDRO_ERR_INVALID_ARG;
+    const InstInfo &I = b->inst[id];
+    // the steps taken once the enqueued launches have run: every launch
+    // steps the instance until its step limit (an instance in its error
+    // state stops earlier; its state is then not meaningful)
+    const long long steps = std::min(I.launched, I.step_end);
+    cudaError_t e = cudaMemcpyAsync(host_dst, I.buf[state_index(I, steps)], I.state_bytes, cudaMemcpyDeviceToHost,
+                                    b->stream);
     return e == cudaSuccess ? HYDRO_OK : HYDRO_ERR_CUDA;
 }
 
 void *hydro_batch_current(hydro_batch *b, int id)
 {
     if (!valid_id(b, id)) return nullptr;
-    return b->inst[id].buf[b->parity];
+    Ctrl c;
+    if (read_inst_ctrl(b, b->inst[id], &c)) return nullptr;
+    return b->inst[id].buf[state_index(b->inst[id], c.step)];
 }
 
 long hydro_batch_launch_count(hydro_batch *b) { return b ? b->launches : -1; }
@@ -634,6 +811,8 @@ int hydro_batch_destroy(hydro_batch *b)
     if (!b) return HYDRO_ERR_INVALID_ARG;
     cudaStreamSynchronize(b->stream);
     drop_graph(b);
+    if (b->staged) cudaEventDestroy(b->staged);
+    if (b->pinned) cudaFreeHost(b->pinned);
     delete b;
     return HYDRO_OK;
 }

@@ -337,18 +337,8 @@ __global__ void __launch_bounds__(TX * TY) ctu2d_kernel(const StepArgs a)
     __shared__ int s_last;
     const double t_now = a.ctrl->t;
     const double dt_cfl = a.ctrl->dt_next;
-    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
-        // U^n carried over
-        constexpr int NV = 4;
-        const int gx = (blockIdx.x % a.tiles_x) * TX + threadIdx.x % TX;
-        const int gy = (blockIdx.x / a.tiles_x) * TY + threadIdx.x / TX;
-        if (gx < a.n[0] && gy < a.n[1])
-            for (int q = 0; q < NV; ++q) {
-                const long long c = q * a.vstride + (long long)gy * a.n[0] + gx;
-                static_cast<T *>(a.Unew)[c] = static_cast<const T *>(a.U)[c];
-            }
-        return;
-    }
+    // frozen: nothing moves (the host finds the current buffer from the step count)
+    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) return;
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;

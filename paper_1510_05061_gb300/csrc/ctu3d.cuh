@@ -525,21 +525,8 @@ __global__ void __launch_bounds__(TX * TY) ctu3d_kernel(const StepArgs a)
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const double t_now = a.ctrl->t;
     const double dt_cfl = a.ctrl->dt_next;
-    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
-        // U^n carried over
-        constexpr int NV = 5;
-        const int nx = a.n[0], ny = a.n[1];
-        const int gx = (tile % a.tiles_x) * TX + threadIdx.x % TX;
-        const int gy = (tile / a.tiles_x) * TY + threadIdx.x / TX;
-        const int zs = chunk * a.zchunk, ze = min(zs + a.zchunk, a.n[2]);
-        if (gx < nx && gy < ny)
-            for (int k = zs; k < ze; ++k)
-                for (int q = 0; q < NV; ++q) {
-                    const long long c = q * a.vstride + (long long)k * a.plane + (long long)gy * nx + gx;
-                    static_cast<T *>(a.Unew)[c] = static_cast<const T *>(a.U)[c];
-                }
-        return;
-    }
+    // frozen: nothing moves (the host finds the current buffer from the step count)
+    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) return;
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;

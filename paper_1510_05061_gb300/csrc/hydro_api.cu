@@ -28,6 +28,8 @@ struct hydro_sim {
     size_t state_bytes;
     void *buf[2];
     int cur;                 // index of the buffer holding the current state
+    int cur0;                // buffer index at step 0: a frozen launch moves nothing, so the state
+                             // after s steps is in buf[(cur0 + s) & 1] (re-read with the control block)
     unsigned char *work;
     WorkLayout lay;
     Ctrl *ctrl;
@@ -292,6 +294,7 @@ int read_ctrl(hydro_sim *s, Ctrl *out)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
     if (out->err) s->err_state = 1;
+    s->cur = (int)((s->cur0 + (out->step & 1)) & 1);
     return HYDRO_OK;
 }
 
@@ -368,6 +371,7 @@ int init_impl(const hydro_problem *prob, void *Ua, void *Ub, void *work, const d
     s->buf[0] = Ua;
     s->buf[1] = Ub;
     s->cur = 0;
+    s->cur0 = 0;
     s->work = static_cast<unsigned char *>(work);
     s->lay = layout(prob);
     s->ctrl = reinterpret_cast<Ctrl *>(s->work + s->lay.ctrl);
@@ -570,6 +574,7 @@ int hydro_set_state(hydro_sim *s, const void *host_src, double t, long step)
     e = cudaMemcpyAsync(s->ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
     s->err_state = 0;
+    s->cur0 = (int)((s->cur + (step & 1)) & 1);
     int rc = recompute_dt(s);
     if (rc) return rc;
     rc = read_ctrl(s, &c);   // also orders the host copies before return

@@ -503,4 +503,28 @@ __device__ __forceinline__ void finish_step(double smax_cta, bool bad_cta, const
     }
 }
 
+// Next work item of a persistent batched launch from list L of the queue
+// for this launch's parity (valid in every thread), or -1 when the list is
+// exhausted.  The CTA that is last to find the list exhausted resets the
+// counters (every other CTA has stopped claiming by then), so the next
+// launch of this parity starts from item 0.  Every thread must call it.
+__device__ __forceinline__ int claim_item(BatchQueue *q, int L, int parity, int *s_it)
+{
+    if (threadIdx.x == 0) {
+        const int n = q->nitems[L];
+        int it = (int)atomicAdd(&q->next[L][parity], 1u);
+        if (it >= n) {
+            it = -1;
+            if (atomicAdd(&q->exited[L][parity], 1u) == gridDim.x - 1) {
+                q->next[L][parity] = 0u;
+                q->exited[L][parity] = 0u;
+                __threadfence();
+            }
+        }
+        *s_it = it;
+    }
+    __syncthreads();
+    return *s_it;
+}
+
 }  // namespace hydro

@@ -93,6 +93,21 @@ struct BatchInst {
     int pad[3];
 };
 
+// Device-resident queue of a batch: the current work lists and their
+// lengths, and per list and launch parity the counter of the next unclaimed
+// item.  The persistent batched kernels read it at run time, so the host
+// changes the batch's membership by rewriting it (stream-ordered copies
+// between launches): the launch arguments, and a captured graph of launches,
+// stay the same.  A launch's CTAs claim items one at a time from the counter
+// (the host orders each list by decreasing item size); the last CTA to run
+// out of items resets the counter and the exit count for the next launch.
+struct BatchQueue {
+    const BatchItem *items[2];   // [0]: 3D items, [1]: 2D items
+    int nitems[2];
+    unsigned next[2][2];         // [list][parity]: next unclaimed item
+    unsigned exited[2][2];       // [list][parity]: CTAs that found no item left
+};
+
 // Workspace layout (offsets in bytes from the workspace base).
 struct WorkLayout {
     size_t ctrl, partial, bg, bgf, stage, red, total;   // stage: first Runge-Kutta stage state

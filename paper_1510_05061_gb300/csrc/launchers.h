@@ -27,22 +27,22 @@ inline bool tile3d_available(int v, bool fp32) { return v >= 0 && v < TILE3D_VAR
 inline bool tile3d_async(int v) { return v >= 4; }
 constexpr int BATCH2D_TX = 32, BATCH2D_TY = 8;
 
-// Persistent batched steps over a device work list; `grid` CTAs walk the
-// items.  *_max_grid: resident CTAs on the current device (SMs x occupancy).
-cudaError_t launch_batch3d_f32(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
-                               int nitems, int parity, int grid, cudaStream_t s);
-cudaError_t launch_batch3d_f64(int variant, bool hse, const BatchInst *insts, const BatchItem *items,
-                               int nitems, int parity, int grid, cudaStream_t s);
+// Persistent batched steps over the device-resident queue's work lists;
+// `grid` CTAs claim the items.  *_max_grid: resident CTAs on the current
+// device (SMs x occupancy).
+cudaError_t launch_batch3d_f32(int variant, bool hse, const BatchInst *insts, BatchQueue *q, int parity, int grid,
+                               cudaStream_t s);
+cudaError_t launch_batch3d_f64(int variant, bool hse, const BatchInst *insts, BatchQueue *q, int parity, int grid,
+                               cudaStream_t s);
 int batch3d_max_grid_f32(int variant, bool hse);
 int batch3d_max_grid_f64(int variant, bool hse);
-inline cudaError_t launch_batch3d(int variant, bool fp32, bool hse, const BatchInst *insts,
-                                  const BatchItem *items, int nitems, int parity, int grid, cudaStream_t s)
+inline cudaError_t launch_batch3d(int variant, bool fp32, bool hse, const BatchInst *insts, BatchQueue *q,
+                                  int parity, int grid, cudaStream_t s)
 {
-    return fp32 ? launch_batch3d_f32(variant, hse, insts, items, nitems, parity, grid, s)
-                : launch_batch3d_f64(variant, hse, insts, items, nitems, parity, grid, s);
+    return fp32 ? launch_batch3d_f32(variant, hse, insts, q, parity, grid, s)
+                : launch_batch3d_f64(variant, hse, insts, q, parity, grid, s);
 }
-cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, const BatchItem *items, int nitems,
-                           int parity, int grid, cudaStream_t s);
+cudaError_t launch_batch2d(bool fp32, const BatchInst *insts, BatchQueue *q, int parity, int grid, cudaStream_t s);
 inline int batch3d_max_grid(int variant, bool fp32, bool hse)
 {
     return fp32 ? batch3d_max_grid_f32(variant, hse) : batch3d_max_grid_f64(variant, hse);

@@ -29,20 +29,6 @@ struct Step2DSmem {
     static constexpr size_t bytes = elems * sizeof(T);
 };
 
-template <typename T, int TX, int TY>
-__device__ __forceinline__ void step2d_copy(const StepArgs &a, int tile, const void *src)
-{
-    constexpr int NV = 4;
-    const int nx = a.n[0], ny = a.n[1];
-    const int gx = (tile % a.tiles_x) * TX + threadIdx.x % TX;
-    const int gy = (tile / a.tiles_x) * TY + threadIdx.x / TX;
-    if (gx < nx && gy < ny)
-        for (int q = 0; q < NV; ++q) {
-            const size_t c = (size_t)q * a.vstride + (size_t)gy * nx + gx;
-            static_cast<T *>(a.Unew)[c] = static_cast<const T *>(src)[c];
-        }
-}
-
 // One CTA's share of a 2D step: tile `tile` (row-major over tiles_x).  ST
 // selects the MUSCL-Hancock step or a Runge-Kutta stage and RC the face
 // states (MC-limited linear or PPM) as in step3d_body.
@@ -309,11 +295,8 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
     __shared__ int s_last;
     const double t_now = a.ctrl->t;
     const double dt_cfl = a.ctrl->dt_next;
-    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
-        if constexpr (ST == STAGE_HANCOCK) step2d_copy<T, TX, TY>(a, blockIdx.x, a.U);
-        if constexpr (ST == STAGE_RK2) step2d_copy<T, TX, TY>(a, blockIdx.x, a.U0);
-        return;
-    }
+    // frozen: nothing moves (the host finds the current buffer from the step count)
+    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) return;
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
@@ -328,19 +311,22 @@ __global__ void __launch_bounds__(TX * TY) step2d_kernel(const StepArgs a)
                     true, &s_last);
 }
 
-// Persistent batched 2D step over a work list of (instance, tile) items; the
-// BatchItem/BatchInst layout is shared with the 3D batch (chunk unused).
+// Persistent batched 2D step over the queue's 2D list of (instance, tile)
+// items; the BatchItem/BatchInst layout is shared with the 3D batch (chunk
+// unused).  Frozen instances are skipped.
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
-step2d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
-                    int nitems, int parity)
+step2d_batch_kernel(const BatchInst *__restrict__ insts, BatchQueue *q, int parity)
 {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    __shared__ int s_last;
+    __shared__ int s_last, s_it;
     __shared__ StepArgs sa;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem *items = q->items[1];
+    for (;;) {
+        const int it = claim_item(q, 1, parity, &s_it);
+        if (it < 0) break;
         const BatchItem w = items[it];
         if (threadIdx.x < (int)(sizeof(StepArgs) / sizeof(int))) {
             reinterpret_cast<int *>(&sa)[threadIdx.x] =
@@ -349,9 +335,7 @@ step2d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
         __syncthreads();
         const double t_now = sa.ctrl->t;
         const double dt_cfl = sa.ctrl->dt_next;
-        if (t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end) {
-            step2d_copy<T, TX, TY>(sa, w.tile, sa.U);
-        } else {
+        if (!(t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end)) {
             const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
             T smax;
             bool bad;

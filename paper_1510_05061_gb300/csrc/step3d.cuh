@@ -115,26 +115,6 @@ __device__ __forceinline__ void cp_async_elem(T *smem_dst, const T *gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Frozen step (time already at t_end, or the handle in its error state):
-// the tile's cells of `src` (U^n) are carried over unchanged.
-template <typename T, int TX, int TY>
-__device__ __forceinline__ void step3d_copy(const StepArgs &a, int tile, int chunk, const void *src)
-{
-    constexpr int NV = 5;
-    const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int gx = (tile % a.tiles_x) * TX + tx, gy = (tile / a.tiles_x) * TY + ty;
-    const int z0 = chunk * a.zchunk, z1 = min(z0 + a.zchunk, nz);
-    const T *U = static_cast<const T *>(src);
-    T *Un = static_cast<T *>(a.Unew);
-    if (gx < nx && gy < ny)
-        for (int k = z0; k < z1; ++k)
-            for (int q = 0; q < NV; ++q) {
-                const size_t c = (size_t)q * a.vstride + (size_t)k * a.plane + (size_t)gy * nx + gx;
-                Un[c] = U[c];
-            }
-}
-
 // One CTA's share of a step: tile `tile` (row-major over tiles_x) of the x-y
 // plane, z planes [chunk*zchunk, min((chunk+1)*zchunk, nz)), time step dtd.
 // On return smax/bad hold this thread's max CFL signal speed and whether one
@@ -728,12 +708,9 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
     // unchanged apart from its error bits)
     const double t_now = a.ctrl->t;
     const double dt_cfl = a.ctrl->dt_next;
-    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) {
-        // U^n carried over: by the step, or by the second stage (from U0)
-        if constexpr (ST == STAGE_HANCOCK) step3d_copy<T, TX, TY>(a, tile, chunk, a.U);
-        if constexpr (ST == STAGE_RK2) step3d_copy<T, TX, TY>(a, tile, chunk, a.U0);
-        return;
-    }
+    // frozen (time at t_end, step limit reached, or error state): nothing
+    // moves; the host finds the current buffer from the step count
+    if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) return;
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax;
     bool bad;
@@ -750,21 +727,24 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
                     true, &s_last);
 }
 
-// Persistent batched step: a fixed grid walks the work list of all
-// instances (item it goes to CTA it mod gridDim.x).  Each instance keeps its
-// own time-control block; the CTA that completes the instance's last item
-// sets that instance's next dt (per-instance CFL).
+// Persistent batched step: a fixed grid claims the items of all instances
+// from the queue's 3D list (largest first).  Each instance keeps its own
+// time-control block; the CTA that completes the instance's last item sets
+// that instance's next dt (per-instance CFL).  A frozen instance (step limit
+// reached, or its error state) is skipped: its state stays where it is.
 template <typename T, bool HSE, int TX, int TY, bool AS = (sizeof(T) == 8)>
 __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY))
-step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items,
-                    int nitems, int parity)
+step3d_batch_kernel(const BatchInst *__restrict__ insts, BatchQueue *q, int parity)
 {
     constexpr int NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    __shared__ int s_last;
+    __shared__ int s_last, s_it;
     __shared__ StepArgs sa;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem *items = q->items[0];
+    for (;;) {
+        const int it = claim_item(q, 0, parity, &s_it);
+        if (it < 0) break;
         const BatchItem w = items[it];
         if (threadIdx.x < (int)(sizeof(StepArgs) / sizeof(int))) {
             reinterpret_cast<int *>(&sa)[threadIdx.x] =
@@ -773,9 +753,7 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__rest
         __syncthreads();
         const double t_now = sa.ctrl->t;
         const double dt_cfl = sa.ctrl->dt_next;
-        if (t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end) {
-            step3d_copy<T, TX, TY>(sa, w.tile, w.chunk, sa.U);
-        } else {
+        if (!(t_now >= sa.t_end || sa.ctrl->err != 0 || sa.ctrl->step >= sa.step_end)) {
             const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
             T smax;
             bool bad;

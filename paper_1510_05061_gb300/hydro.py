@@ -47,7 +47,8 @@ EXPORTS = (
     "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
     "hydro_selftest_math", "hydro_selftest_device_once", "hydro_fma_probe", "hydro_fma_probe_flops", "hydro_batch_workspace_bytes", "hydro_batch_init",
     "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
-    "hydro_batch_create", "hydro_batch_add", "hydro_batch_remove", "hydro_batch_set_graph",
+    "hydro_batch_create", "hydro_batch_add", "hydro_batch_add_async", "hydro_batch_remove",
+    "hydro_batch_remove_async", "hydro_batch_get_state_async", "hydro_batch_set_graph",
     "hydro_batch_configure", "hydro_batch_variant_shape", "hydro_batch_step", "hydro_batch_reduce",
     "hydro_batch_get_fields", "hydro_batch_get_state", "hydro_batch_current", "hydro_batch_launch_count", "hydro_batch_items",
     "hydro_batch_destroy", "hydro_checkpoint_save", "hydro_checkpoint_load", "hydro_slab_extent", "hydro_slab_state_bytes", "hydro_slab_workspace_bytes",
@@ -145,6 +146,12 @@ def load(path: str = LIB_PATH):
     L.hydro_batch_add.argtypes = [vp, P, vp, vp, vp, D, D, C.c_long, C.POINTER(C.c_int)]
     L.hydro_batch_remove.restype = C.c_int
     L.hydro_batch_remove.argtypes = [vp, C.c_int]
+    L.hydro_batch_add_async.restype = C.c_int
+    L.hydro_batch_add_async.argtypes = [vp, P, vp, vp, vp, vp, D, C.c_long, C.POINTER(C.c_int)]
+    L.hydro_batch_remove_async.restype = C.c_int
+    L.hydro_batch_remove_async.argtypes = [vp, C.c_int]
+    L.hydro_batch_get_state_async.restype = C.c_int
+    L.hydro_batch_get_state_async.argtypes = [vp, C.c_int, vp]
     L.hydro_batch_set_graph.restype = C.c_int
     L.hydro_batch_set_graph.argtypes = [vp, C.c_int]
     L.hydro_batch_configure.restype = C.c_int

@@ -3,12 +3,20 @@
 Requests (2D Kelvin-Helmholtz and 3D Rayleigh-Taylor solves of different
 sizes, each for a given number of steps) arrive over time.  The server keeps
 every admitted solve's state on the device and advances all of them together:
-each tick is one batched step (one persistent launch over the device work
-list for the 3D solves, one for the 2D solves).  A request is admitted as
-soon as it has arrived, a slot is free and its device memory (two state
-buffers and its work buffer) fits the HBM budget; finished solves leave the
-batch at the end of the tick that completes them, which frees their slot and
-memory for waiting requests.  Latency is completion time minus arrival time.
+each step is one batched step (one persistent launch for the 3D solves, one
+for the 2D solves, whose CTAs claim work items from the batch's
+device-resident queue).  A request is admitted as soon as it has arrived, a
+slot is free and its device memory (two state buffers and its work buffer)
+fits the HBM budget; it leaves the batch right after the step that completes
+it.  The host never waits for the whole stream: admissions (an asynchronous
+copy of the initial fields from pinned memory and the device conversion),
+retirements (an asynchronous copy of the result to pinned memory and the
+removal from the device queue) and the steps are all enqueued on the batch
+stream, and the host only polls events, keeping up to `lookahead` steps in
+flight.  Each request's step limit lives in the device instance table, so a
+solve that finishes inside an enqueued run of steps stops there by itself.
+Latency is the time the host sees a request's completion event minus its
+arrival time.
 
 The paper motivates this as capacity computing: large suites of simulations
 for parameter studies and uncertainty quantification ("Increasing computing
@@ -43,6 +51,8 @@ class Request:
     done: float = math.nan
     slot: int = -1
     result: Optional[np.ndarray] = None
+    first_launch: int = 0             # batched steps enqueued before the request joined
+    result_pinned: Optional[object] = None
 
     @property
     def work(self) -> int:
@@ -114,11 +124,13 @@ class PayloadPrefetcher:
 
 
 class Server:
-    """Admission by slots and HBM budget, one batched step per tick."""
+    """Admission by slots and HBM budget; steps, admissions and retirements
+    enqueued on one stream without synchronising it."""
 
     def __init__(self, budget_bytes: float = 150e9, max_active: int = 64,
                  precision: int = inputs.FP32, max_items3d: Optional[int] = None,
-                 max_items2d: Optional[int] = None, use_graph: bool = False, stream=None):
+                 max_items2d: Optional[int] = None, use_graph: bool = True, stream=None,
+                 lookahead: int = 8, chunk: int = 2):
         import torch
 
         self.torch = torch
@@ -126,6 +138,8 @@ class Server:
         self.used = 0.0
         self.max_active = max_active
         self.precision = precision
+        self.lookahead = max(1, int(lookahead))
+        self.chunk = max(1, int(chunk))
         self.stream = stream if stream is not None else torch.cuda.Stream()
         dev = torch.device("cuda", torch.cuda.current_device())
         self.dev = dev
@@ -138,7 +152,8 @@ class Server:
             p, _ = inputs.kelvin_helmholtz(2048, ndim=2, precision=precision)
             max_items2d = max_active * hydro.load().hydro_problem_max_items(hydro.make_problem(p))
         nbytes = hydro.load().hydro_batch_create_bytes(max_active, int(max_items3d), int(max_items2d))
-        self._work = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(self.stream):
+            self._work = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
         wptr = (self._work.data_ptr() + 255) // 256 * 256
         h = hydro.C.c_void_p()
         hydro._check(hydro.load().hydro_batch_create(max_active, int(max_items3d), int(max_items2d), precision,
@@ -149,9 +164,10 @@ class Server:
         hydro._check(hydro.load().hydro_batch_set_graph(h, 1 if use_graph else 0), "hydro_batch_set_graph")
         self.active: Dict[int, Request] = {}
         self._bufs: Dict[int, list] = {}
-        self._steps: Dict[int, int] = {}
+        self.launched = 0            # batched steps enqueued so far
+        self._marks = collections.deque()   # (event, launched, requests retired with it, keepalive)
+        self._timing = []            # (start event, end event, zone-updates, bytes) per enqueued run
         self.ticks = 0
-        self.busy_s = 0.0
         self.zone_updates = 0
         self.bytes_moved = 0
 
@@ -161,6 +177,9 @@ class Server:
         return 2 * hydro.hydro_state_bytes(cp) + hydro.load().hydro_instance_work_bytes(cp)
 
     def try_admit(self, req: Request, now: float) -> bool:
+        """Admit `req` if a slot and memory are free: its buffers are taken
+        from the stream's memory pool, its initial fields copied from pinned
+        memory and converted on the device, all enqueued on the stream."""
         if len(self.active) >= self.max_active:
             return False
         need = self.request_bytes(req)
@@ -170,56 +189,102 @@ class Server:
         cp = hydro.make_problem(req.prob)
         sb = hydro.hydro_state_bytes(cp)
         wb = hydro.load().hydro_instance_work_bytes(cp)
-        bufs = [torch.empty(n + 256, dtype=torch.uint8, device=self.dev) for n in (sb, sb, wb)]
+        # memory allocated on the batch stream: once freed, the caching
+        # allocator hands it out again only to work ordered after what was
+        # enqueued on this stream, so buffers of a removed solve need no wait
+        with torch.cuda.stream(self.stream):
+            bufs = [torch.empty(n + 256, dtype=torch.uint8, device=self.dev) for n in (sb, sb, wb)]
+            W = np.ascontiguousarray(req.W, dtype=np.float64)
+            w_pin = torch.from_numpy(W).pin_memory()
+            w_dev = torch.empty(W.shape, dtype=torch.float64, device=self.dev)
+            w_dev.copy_(w_pin, non_blocking=True)
         ptrs = [(b.data_ptr() + 255) // 256 * 256 for b in bufs]
         bg = hydro.background_tables(req.prob)
-        W = np.ascontiguousarray(req.W, dtype=np.float64)
         sid = hydro.C.c_int(-1)
-        rc = hydro.load().hydro_batch_add(self.h, hydro.C.byref(cp), hydro.C.c_void_p(ptrs[0]),
-                                          hydro.C.c_void_p(ptrs[1]), hydro.C.c_void_p(ptrs[2]),
-                                          hydro._dptr(W), hydro._dptr(bg), req.steps, hydro.C.byref(sid))
+        rc = hydro.load().hydro_batch_add_async(self.h, hydro.C.byref(cp), hydro.C.c_void_p(ptrs[0]),
+                                                hydro.C.c_void_p(ptrs[1]), hydro.C.c_void_p(ptrs[2]),
+                                                hydro.C.c_void_p(w_dev.data_ptr()), hydro._dptr(bg), req.steps,
+                                                hydro.C.byref(sid))
         if rc == hydro.HYDRO_ERR_OOM:
             return False
-        hydro._check(rc, "hydro_batch_add")
+        hydro._check(rc, "hydro_batch_add_async")
+        # the pinned copy must outlive its transfer: released with the next mark
+        self._pending_keep = getattr(self, "_pending_keep", []) + [w_pin, w_dev]
         req.slot = sid.value
         req.admit = now
+        req.first_launch = self.launched
         self.active[req.slot] = req
         self._bufs[req.slot] = bufs
-        self._steps[req.slot] = 0
         self.used += need
         return True
 
-    def tick(self) -> List[Request]:
-        """One step of every active solve; returns the solves it finished."""
-        t0 = time.perf_counter()
-        hydro._check(hydro.load().hydro_batch_step(self.h, 1), "hydro_batch_step")
-        self.stream.synchronize()
-        self.busy_s += time.perf_counter() - t0
-        self.ticks += 1
-        finished = []
-        for sid, req in list(self.active.items()):
-            self._steps[sid] += 1
-            b = 4 if self.precision == inputs.FP32 else 8
-            self.zone_updates += req.prob.ncell
-            self.bytes_moved += 2 * req.prob.nvar * b * req.prob.ncell
-            if self._steps[sid] >= req.steps:
-                finished.append(req)
+    def _steps_to_next_finish(self) -> int:
+        return min(r.first_launch + r.steps - self.launched for r in self.active.values())
+
+    def advance(self, keep_results: Callable[[Request], bool]) -> List[Request]:
+        """Enqueue the steps up to the next completion (at most `chunk`), then
+        the retirement of every solve they complete; returns those solves
+        (complete once the mark recorded with them has been passed)."""
+        torch = self.torch
+        k = max(1, min(self.chunk, self._steps_to_next_finish()))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        hydro._check(hydro.load().hydro_batch_step(self.h, k), "hydro_batch_step")
+        e1.record(self.stream)
+        b = 4 if self.precision == inputs.FP32 else 8
+        zu = sum(r.prob.ncell * min(k, r.first_launch + r.steps - self.launched) for r in self.active.values())
+        by = sum(2 * r.prob.nvar * b * r.prob.ncell * min(k, r.first_launch + r.steps - self.launched)
+                 for r in self.active.values())
+        self._timing.append((e0, e1, zu, by))
+        self.launched += k
+        self.ticks += k
+        finished = [r for r in self.active.values() if r.first_launch + r.steps <= self.launched]
+        keep = list(getattr(self, "_pending_keep", []))
+        self._pending_keep = []
+        for req in finished:
+            if keep_results(req):
+                dt = np.float32 if self.precision == inputs.FP32 else np.float64
+                out = torch.empty(tuple(req.prob.shape), dtype=torch.float32 if dt == np.float32 else torch.float64,
+                                  pin_memory=True)
+                hydro._check(hydro.load().hydro_batch_get_state_async(self.h, req.slot,
+                                                                      hydro.C.c_void_p(out.data_ptr())),
+                             "hydro_batch_get_state_async")
+                req.result_pinned = out
+            hydro._check(hydro.load().hydro_batch_remove_async(self.h, req.slot), "hydro_batch_remove_async")
+            del self.active[req.slot]
+            keep.append(self._bufs.pop(req.slot))
+            self.used -= self.request_bytes(req)
+        mark = torch.cuda.Event()
+        mark.record(self.stream)
+        self._marks.append((mark, self.launched, finished, keep))
         return finished
 
-    def get_state(self, req: Request) -> np.ndarray:
-        out = np.empty(req.prob.shape, dtype=np.float32 if self.precision == inputs.FP32 else np.float64)
-        hydro._check(hydro.load().hydro_batch_get_state(self.h, req.slot, hydro.C.c_void_p(out.ctypes.data)),
-                     "hydro_batch_get_state")
-        return out
+    def poll(self, block: bool = False) -> List[Request]:
+        """Requests whose completion the device has reached (the oldest mark
+        is waited for when `block`)."""
+        done = []
+        while self._marks:
+            mark, launched, reqs, keep = self._marks[0]
+            if not mark.query():
+                if not block:
+                    break
+                mark.synchronize()
+                block = False
+            self._marks.popleft()
+            for r in reqs:
+                if getattr(r, "result_pinned", None) is not None:
+                    r.result = r.result_pinned.numpy().copy()
+                    r.result_pinned = None
+            done.extend(reqs)
+        return done
 
-    def retire(self, req: Request, keep_result: bool = False):
-        if keep_result:
-            req.result = self.get_state(req)
-        hydro._check(hydro.load().hydro_batch_remove(self.h, req.slot), "hydro_batch_remove")
-        del self.active[req.slot]
-        del self._bufs[req.slot]
-        del self._steps[req.slot]
-        self.used -= self.request_bytes(req)
+    def in_flight(self) -> int:
+        """Enqueued steps the device has not passed yet (by the oldest open mark)."""
+        return self.launched - self._marks[0][1] + self.chunk if self._marks else 0
+
+    def busy_seconds(self) -> float:
+        return sum(a.elapsed_time(b) for a, b, _, _ in self._timing) * 1e-3
 
     def run(self, requests: List[Request], keep_results: Callable[[Request], bool] = lambda r: False,
             time_scale: float = 1.0) -> dict:
@@ -229,7 +294,7 @@ class Server:
         finished: List[Request] = []
         launches0 = hydro.load().hydro_batch_launch_count(self.h)
         t0 = time.perf_counter()
-        while pending or self.active:
+        while pending or self.active or self._marks:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival * time_scale <= now:
                 lazy = prefetch is not None and pending[0].id in prefetch.ids
@@ -240,15 +305,18 @@ class Server:
                 if lazy:
                     prefetch.release(pending[0])
                 pending.popleft()
-            if not self.active:
-                if pending:
-                    time.sleep(max(0.0, min(pending[0].arrival * time_scale - now, 0.01)))
-                continue
-            for req in self.tick():
+            if self.active:
+                self.advance(keep_results)
+            for req in self.poll(block=self.in_flight() > self.lookahead or (not self.active and not pending)):
                 req.done = time.perf_counter() - t0
-                self.retire(req, keep_results(req))
                 finished.append(req)
+            if not self.active and not self._marks and pending:
+                time.sleep(max(0.0, min(pending[0].arrival * time_scale - (time.perf_counter() - t0), 0.01)))
         makespan = time.perf_counter() - t0
+        self.torch.cuda.synchronize()
+        busy = self.busy_seconds()
+        self.zone_updates = sum(t[2] for t in self._timing)
+        self.bytes_moved = sum(t[3] for t in self._timing)
         lat = np.array([r.done - r.arrival * time_scale for r in finished])
         work = sum(r.work for r in finished)
         return {
@@ -258,9 +326,9 @@ class Server:
             "makespan_s": makespan,
             "zone_updates": work,
             "zone_updates_per_s": work / makespan,
-            "busy_s": self.busy_s,
-            "busy_zone_updates_per_s": self.zone_updates / self.busy_s if self.busy_s else None,
-            "busy_hbm_gbs": self.bytes_moved / self.busy_s / 1e9 if self.busy_s else None,
+            "busy_s": busy,
+            "busy_zone_updates_per_s": self.zone_updates / busy if busy else None,
+            "busy_hbm_gbs": self.bytes_moved / busy / 1e9 if busy else None,
             "ticks": self.ticks,
             "launches": hydro.load().hydro_batch_launch_count(self.h) - launches0,
         }
@@ -270,6 +338,7 @@ class Server:
             hydro.load().hydro_batch_destroy(self.h)
             self.h = None
         self._bufs = {}
+        self._marks.clear()
 
     def __del__(self):
         try:

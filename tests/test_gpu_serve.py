@@ -52,16 +52,16 @@ def test_served_results_equal_solo_and_budget_binds(env):
     budget = 2.2 * max(sizes)            # at most a few solves fit at once
     srv = serve.Server(budget_bytes=budget, max_active=8, max_items3d=200000, max_items2d=20000)
     peak = {"n": 0, "mixed": False}
-    orig_tick = srv.tick
+    orig_advance = srv.advance
 
-    def tick():
+    def advance(keep):
         peak["n"] = max(peak["n"], len(srv.active))
         fams = {r.family for r in srv.active.values()}
         peak["mixed"] |= len(fams) == 2
         assert srv.used <= budget
-        return orig_tick()
+        return orig_advance(keep)
 
-    srv.tick = tick
+    srv.advance = advance
     stats = srv.run(reqs, keep_results=lambda r: True)
     srv.close()
     assert stats["requests"] == len(reqs)
@@ -77,13 +77,13 @@ def test_slot_limit_and_reuse(env):
     reqs = small_requests(serve)[:5]
     srv = serve.Server(budget_bytes=1e12, max_active=2, max_items3d=200000, max_items2d=20000)
     seen = []
-    orig = srv.tick
+    orig = srv.advance
 
-    def tick():
+    def advance(keep):
         seen.append(len(srv.active))
-        return orig()
+        return orig(keep)
 
-    srv.tick = tick
+    srv.advance = advance
     stats = srv.run(reqs, keep_results=lambda r: True)
     srv.close()
     assert max(seen) <= 2 and stats["requests"] == 5
@@ -108,3 +108,48 @@ def test_lazy_payloads_match_eager(env):
     assert all(r.W is None for r in lazy)
     for i in out[0]:
         assert np.array_equal(out[0][i], out[1][i])
+
+
+def test_served_results_match_the_oracle(env):
+    """A served FP32 result against the FP64 oracle: density within the
+    FP32 accuracy bound (L1-relative 1e-4) after the request's steps."""
+    import oracle
+
+    torch, hydro, serve = env
+    reqs = small_requests(serve)[:4]
+    srv = serve.Server(budget_bytes=1e12, max_active=4, max_items3d=200000, max_items2d=20000)
+    srv.run(reqs, keep_results=lambda r: True)
+    srv.close()
+    oracle.build()
+    for r in reqs:
+        o = oracle.Oracle(r.prob.replace(precision=inputs.FP64))
+        V, _, s, _ = o.run(o.state_from_prim(r.W), max_steps=r.steps)
+        assert s == r.steps
+        rho = o.total(V)[0]
+        rho_gpu = o.total(r.result.astype(np.float64))[0]
+        err = float(np.abs(rho_gpu - rho).sum() / np.abs(rho).sum())
+        assert err <= 1e-4, (r.id, err)
+
+
+def test_server_loop_never_waits_for_the_whole_stream(env, monkeypatch):
+    """Steps, admissions and retirements are enqueued without synchronising
+    the stream; the host only polls (or waits on) its own marks."""
+    torch, hydro, serve = env
+    reqs = small_requests(serve)
+    calls = {"n": 0}
+
+    def counted(orig):
+        def f(*a, **k):
+            calls["n"] += 1
+            return orig(*a, **k)
+        return f
+
+    srv = serve.Server(budget_bytes=1e12, max_active=3, max_items3d=200000, max_items2d=20000)
+    monkeypatch.setattr(srv.stream, "synchronize", counted(srv.stream.synchronize))
+    monkeypatch.setattr(torch.cuda, "synchronize", counted(torch.cuda.synchronize))
+    stats = srv.run(reqs, keep_results=lambda r: True)
+    srv.close()
+    assert stats["requests"] == len(reqs)
+    assert calls["n"] <= 1            # the statistics' final synchronisation only
+    for r in reqs:
+        assert np.array_equal(r.result, solo_state(hydro, r)), r.id
