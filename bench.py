@@ -67,6 +67,8 @@ FLOPS_PER_ZONE_2D_CTU = 10 + 40 + 2 * 25 + 32 + 128 + 2 * 2 * 26 + 128 + 42 + 19
 
 # tile shape of each 3D variant; variants 4..7 stage the next plane asynchronously
 TILE_NAMES = {0: "32, 8", 1: "32, 4", 2: "16, 16", 3: "32, 16", 4: "32, 8", 5: "32, 4", 6: "16, 16", 7: "32, 16"}
+# paired-cell FP32 variants: threads (x, y) per tile (two x-adjacent cells per thread)
+PAIR_THREADS = {8: (16, 16), 9: (16, 8), 10: (8, 16)}
 
 CONFIGS = {
     # name: (builder, description, precision, hse)
@@ -132,6 +134,12 @@ def step_kernel_names(prob, variant: int):
     if prob.scheme == inputs.CTU:
         return [f"ctu3d_kernel<{tname}, {prob.hse_subtract}, 16, {16 if itemsize == 4 else 8}>" if prob.ndim == 3
                 else f"ctu2d_kernel<{tname}, 32, 8>"]
+    if prob.ndim == 3 and variant in PAIR_THREADS and not rk2 and itemsize == 4:
+        # paired-cell FP32 MUSCL-Hancock step: threads (x, y) of the tile
+        pgz = int(bool(prob.hse_subtract or (prob.grav[0] == 0 and prob.grav[1] == 0)))
+        txp, typ = PAIR_THREADS[variant]
+        minb = 1 if variant == 8 else 3
+        return [f"step3d_pair_kernel<{prob.hse_subtract}, {txp}, {typ}, {pgz}, {minb}>"]
     return [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}, {gz}>"
              if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
 
@@ -773,10 +781,18 @@ def run_gpu(args):
     # ---- device-resident run: inputs in HBM before the timed region
     sim = hydro.Simulation(prob, W, stream=stream)
     tune = None
-    if not args.no_tune and prob.ndim == 3:
+    if args.variant is not None and prob.ndim == 3:
+        # a fixed tile variant and z-chunk (profiling runs)
+        tune = {"variant": args.variant, "zchunk": args.zchunk, "cached": False, "note": "fixed by --variant"}
+        sim.close()
+        sim = hydro.Simulation(prob, W, stream=stream)
+        sim.configure(tune["variant"], tune["zchunk"])
+    elif not args.no_tune and prob.ndim == 3:
         from paper_1510_05061_gb300 import autotune
 
         tune = autotune.tune_simulation(sim, use_cache=not args.retune)
+        if args.show_tuning:
+            print(json.dumps({"autotune_table": tune.get("table")}), file=sys.stderr, flush=True)
         tune = {k: v for k, v in tune.items() if k != "table"}
         # tuning advanced the solve: start the measured run from the initial state
         sim.close()
@@ -973,6 +989,9 @@ def main():
                     help="dram bytes per launch of the step kernel from an ncu capture")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-tune", action="store_true", help="default tile shape and z-chunk")
+    ap.add_argument("--variant", type=int, default=None, help="single 3D solves: fixed tile variant (no tuning)")
+    ap.add_argument("--zchunk", type=int, default=0, help="with --variant: z-chunk (0 = default)")
+    ap.add_argument("--show-tuning", action="store_true", help="print the autotuner's timing table to stderr")
     ap.add_argument("--requests", type=int, default=200, help="served configs: number of requests")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served configs: HBM budget")
     ap.add_argument("--max-active", type=int, default=64, help="served configs: concurrent solves")

@@ -192,8 +192,18 @@ int hydro_set_zchunk(hydro_sim *sim, int zchunk);
    one plane ahead (MUSCL-Hancock step; the other integrators use the shape
    only).  Default: variant 7 (32 x 16) for FP32, 6 (16 x 16) for FP64, the
    autotuner's usual choices on GB300.  Variants 3
-   and 7 (32 x 16) are FP32 only.  Results do not depend on the choice. */
+   and 7 (32 x 16) are FP32 only.  Results do not depend on the choice
+   among 0..7; the paired-cell FP32 variants 8..10 are described below. */
 int hydro_set_tile(hydro_sim *sim, int variant);
+
+/* Paired-cell FP32 tiles: variants 8, 9, 10 (32 x 16, 32 x 8 and 16 x 16
+   cells) run the FP32 MUSCL-Hancock step with each thread owning two
+   x-adjacent cells, in packed f32x2 arithmetic (FP32, HYDRO_SCHEME_HANCOCK,
+   3D single solves only).  Their results do not depend on the choice among
+   8..10, and differ from those of variants 0..7 by FP32 rounding only (the
+   same formulas, grouped into other instructions).  hydro_tile_shape gives
+   the cell tile (tx x ty) of any single-solve variant 0..10. */
+int hydro_tile_shape(int variant, int *tx, int *ty);
 
 /* Number of kernels launched by this handle so far. */
 long hydro_launch_count(hydro_sim *sim);

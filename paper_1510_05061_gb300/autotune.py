@@ -123,7 +123,7 @@ def sim_signature(sim) -> str:
     scheme = {inputs.SSPRK2: "rk2", inputs.CTU: "ctu"}.get(getattr(p, "scheme", 0), "hancock")
     if getattr(p, "recon", 0) == inputs.PPM:
         scheme += "-ppm"
-    return (f"{torch.cuda.get_device_name()}|single|{prec}|hse{p.hse_subtract}|{scheme}"
+    return (f"{torch.cuda.get_device_name()}|single-v2|{prec}|hse{p.hse_subtract}|{scheme}"
             f"|n={p.n[0]}x{p.n[1]}x{p.n[2]}")
 
 
@@ -156,8 +156,8 @@ def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 1
         ch = cache[key]
         sim.configure(ch["variant"], ch["zchunk"])
         return dict(ch, cached=True)
-    shapes = hydro.batch_variants()
-    variants = list(range(len(shapes))) if variants is None else list(variants)
+    shapes = dict(hydro.sim_variants())
+    variants = sorted(shapes) if variants is None else list(variants)
     table, best = [], None
     for v in variants:
         for z in zchunks:
@@ -169,8 +169,8 @@ def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 1
                 break
             sim.run_steps(2)
             ms = time_sim_steps(sim, steps)
-            table.append({"variant": v, "tile": list(shapes[v]), "async_staging": v >= 4, "zchunk": z,
-                          "ms_per_step": ms})
+            table.append({"variant": v, "tile": list(shapes[v]), "async_staging": 4 <= v < 8,
+                          "paired_cells": v in hydro.PAIR_VARIANTS, "zchunk": z, "ms_per_step": ms})
             if best is None or ms < best["ms_per_step"]:
                 best = table[-1]
     sim.configure(best["variant"], best["zchunk"])

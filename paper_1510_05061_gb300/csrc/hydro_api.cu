@@ -108,6 +108,8 @@ int step_max_ctas(const hydro_problem *p)
     for (int v = 0; v < TILE3D_VARIANTS; ++v)
         m = std::max(m, tiles_along(p->n[0], TILE3D_SHAPES[v].tx) * tiles_along(p->n[1], TILE3D_SHAPES[v].ty) *
                             p->n[2]);
+    for (int v = 0; v < PAIR_VARIANTS; ++v)
+        m = std::max(m, tiles_along(p->n[0], PAIR_SHAPES[v].tx) * tiles_along(p->n[1], PAIR_SHAPES[v].ty) * p->n[2]);
     if (p->scheme == HYDRO_SCHEME_CTU)
         m = std::max(m, (int)ctu3d_blocks(p->n, p->precision == HYDRO_FP32));
     return m;
@@ -257,6 +259,8 @@ cudaError_t launch_kernel(hydro_sim *s, const StepArgs &a, int stage)
         return launch_step2d(a, dim3(s->tiles_x * s->tiles_y, 1), s->stream, fp32, stage, recon);
     if (s->prob.scheme == HYDRO_SCHEME_CTU) return launch_ctu3d(a, s->stream, fp32, hse);
     const dim3 grid(s->tiles_x * s->tiles_y, (s->prob.n[2] + s->zchunk - 1) / s->zchunk);
+    if (stage == STAGE_HANCOCK && pair_variant(s->variant))
+        return launch_pair3d(s->variant - PAIR_VARIANT0, a, grid, s->stream, hse);
     if (stage == STAGE_HANCOCK)
         return fp32 ? launch_step3d_f32(s->variant, a, grid, s->stream, hse)
                     : launch_step3d_f64(s->variant, a, grid, s->stream, hse);
@@ -623,10 +627,27 @@ int hydro_set_tile(hydro_sim *s, int variant)
 {
     if (!s) return HYDRO_ERR_INVALID_ARG;
     if (s->prob.ndim == 2) return variant == 0 ? HYDRO_OK : HYDRO_ERR_INVALID_ARG;
-    if (!tile3d_available(variant, s->prob.precision == HYDRO_FP32)) return HYDRO_ERR_INVALID_ARG;
+    const bool fp32 = s->prob.precision == HYDRO_FP32;
+    if (pair_variant(variant)) {
+        // paired-cell tiles: FP32 MUSCL-Hancock only
+        if (!fp32 || s->prob.scheme != HYDRO_SCHEME_HANCOCK) return HYDRO_ERR_INVALID_ARG;
+    } else if (!tile3d_available(variant, fp32)) {
+        return HYDRO_ERR_INVALID_ARG;
+    }
+    // the other integrators take only the shape of variants 0..7
+    if (s->prob.scheme != HYDRO_SCHEME_HANCOCK && pair_variant(variant)) return HYDRO_ERR_INVALID_ARG;
     s->variant = variant;
-    s->tiles_x = tiles_along(s->prob.n[0], TILE3D_SHAPES[variant].tx);
-    s->tiles_y = tiles_along(s->prob.n[1], TILE3D_SHAPES[variant].ty);
+    s->tiles_x = tiles_along(s->prob.n[0], tile_shape(variant).tx);
+    s->tiles_y = tiles_along(s->prob.n[1], tile_shape(variant).ty);
+    return HYDRO_OK;
+}
+
+int hydro_tile_shape(int variant, int *tx, int *ty)
+{
+    if (!tx || !ty || !(pair_variant(variant) || (variant >= 0 && variant < TILE3D_VARIANTS)))
+        return HYDRO_ERR_INVALID_ARG;
+    *tx = tile_shape(variant).tx;
+    *ty = tile_shape(variant).ty;
     return HYDRO_OK;
 }
 

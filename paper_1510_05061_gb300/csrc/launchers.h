@@ -24,6 +24,14 @@ constexpr int TILE3D_VARIANTS = 8;
 constexpr TileShape TILE3D_SHAPES[TILE3D_VARIANTS] = {{32, 8}, {32, 4}, {16, 16}, {32, 16},
                                                       {32, 8}, {32, 4}, {16, 16}, {32, 16}};
 inline bool tile3d_available(int v, bool fp32) { return v >= 0 && v < TILE3D_VARIANTS && (v % 4 != 3 || fp32); }
+// Paired-cell tiles (FP32 MUSCL-Hancock single solves only): variants
+// PAIR_VARIANT0 + pv, each thread owning two x-adjacent cells of a tile of
+// PAIR_SHAPES[pv] cells.
+constexpr int PAIR_VARIANT0 = 8, PAIR_VARIANTS = 3;
+constexpr TileShape PAIR_SHAPES[PAIR_VARIANTS] = {{32, 16}, {32, 8}, {16, 16}};
+inline bool pair_variant(int v) { return v >= PAIR_VARIANT0 && v < PAIR_VARIANT0 + PAIR_VARIANTS; }
+// cell tile of any 3D single-solve variant
+inline TileShape tile_shape(int v) { return pair_variant(v) ? PAIR_SHAPES[v - PAIR_VARIANT0] : TILE3D_SHAPES[v]; }
 inline bool tile3d_async(int v) { return v >= 4; }
 constexpr int BATCH2D_TX = 32, BATCH2D_TY = 8;
 
@@ -49,6 +57,8 @@ inline int batch3d_max_grid(int variant, bool fp32, bool hse)
 }
 int batch2d_max_grid(bool fp32);
 
+// paired-cell FP32 MUSCL-Hancock step, pair variant pv (grid = tiles x z-chunks)
+cudaError_t launch_pair3d(int pv, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
 // single-solve 3D step with tile variant v (grid = tiles x z-chunks)
 cudaError_t launch_step3d_f64(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);
 cudaError_t launch_step3d_f32(int v, const StepArgs &a, dim3 grid, cudaStream_t s, bool hse);

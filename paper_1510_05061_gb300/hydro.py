@@ -44,7 +44,7 @@ EXPORTS = (
     "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_init_conserved", "hydro_step",
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
     "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk", "hydro_set_tile",
-    "hydro_launch_count", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
+    "hydro_launch_count", "hydro_tile_shape", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
     "hydro_selftest_math", "hydro_selftest_device_once", "hydro_fma_probe", "hydro_fma_probe_flops", "hydro_batch_workspace_bytes", "hydro_batch_init",
     "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
     "hydro_batch_create", "hydro_batch_add", "hydro_batch_add_async", "hydro_batch_remove",
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH):
     L.hydro_set_tile.argtypes = [vp, C.c_int]
     L.hydro_launch_count.restype = C.c_long
     L.hydro_launch_count.argtypes = [vp]
+    L.hydro_tile_shape.restype = C.c_int
+    L.hydro_tile_shape.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.hydro_destroy.restype = C.c_int
     L.hydro_destroy.argtypes = [vp]
     L.hydro_strerror.restype = C.c_char_p
@@ -514,6 +516,27 @@ def hydro_batch_variant_shape(v: int):
     tx, ty = C.c_int(), C.c_int()
     _check(load().hydro_batch_variant_shape(int(v), C.byref(tx), C.byref(ty)), "hydro_batch_variant_shape")
     return tx.value, ty.value
+
+
+# paired-cell FP32 MUSCL-Hancock tile variants of single 3D solves
+PAIR_VARIANTS = (8, 9, 10)
+
+
+def tile_shape(variant: int):
+    """Cell tile (tx, ty) of a single-solve 3D variant (0..10)."""
+    tx, ty = C.c_int(), C.c_int()
+    _check(load().hydro_tile_shape(int(variant), C.byref(tx), C.byref(ty)), "hydro_tile_shape")
+    return tx.value, ty.value
+
+
+def sim_variants():
+    """Variant indices of single 3D solves with their cell tiles."""
+    out = []
+    for v in range(0, 11):
+        tx, ty = C.c_int(), C.c_int()
+        if load().hydro_tile_shape(v, C.byref(tx), C.byref(ty)) == HYDRO_OK:
+            out.append((v, (tx.value, ty.value)))
+    return out
 
 
 def batch_variants():
