@@ -138,7 +138,7 @@ def step_kernel_names(prob, variant: int):
         # paired-cell FP32 MUSCL-Hancock step: threads (x, y) of the tile
         pgz = int(bool(prob.hse_subtract or (prob.grav[0] == 0 and prob.grav[1] == 0)))
         txp, typ = PAIR_THREADS[variant]
-        minb = 1 if variant == 8 else 3
+        minb = 2 if variant == 8 else 3
         return [f"step3d_pair_kernel<{prob.hse_subtract}, {txp}, {typ}, {pgz}, {minb}>"]
     return [(f"step3d_kernel<{tname}, {prob.hse_subtract}, {tile}, {st}, {prob.recon}, {async_flag}, {gz}>"
              if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
@@ -173,12 +173,15 @@ def measured_traffic(config: str, kernel: str):
     return float(e["bytes_per_launch"])
 
 
-def record_traffic(config: str, csv_path: str) -> int:
+def record_traffic(config: str, csv_path: str, scale: float = 1.0, note: str = "") -> int:
     """Read an ncu CSV (--csv --log-file) of this benchmark taken with
     --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,
     store each kernel's mean DRAM bytes per launch for `config` in
     profiles/traffic.json (with the current source hash) and print the launch
-    list (launches, device time, share, traffic) as a markdown table."""
+    list (launches, device time, share, traffic) as a markdown table.  With
+    scale != 1 the capture was taken on a smaller grid of the workload and
+    its bytes are scaled to the workload's cells (traffic proportional to
+    the cells processed); `note` says so in the table."""
     import csv
     import re
 
@@ -207,8 +210,10 @@ def record_traffic(config: str, csv_path: str) -> int:
         byts = [m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0) for m in launches.values()]
         rows.append((name, len(launches), ns, sum(byts) / len(byts)))
         total_ns += ns
-        table.setdefault(config, {})[name] = {"bytes_per_launch": sum(byts) / len(byts),
-                                              "launches": len(launches), "source_sha": sha}
+        entry = {"bytes_per_launch": scale * sum(byts) / len(byts), "launches": len(launches), "source_sha": sha}
+        if scale != 1.0:
+            entry["scaled"] = note or f"captured on a smaller grid, bytes x {scale:g}"
+        table.setdefault(config, {})[name] = entry
     with open(path, "w") as fh:
         json.dump(table, fh, indent=1, sort_keys=True)
     print("| kernel | launches | device time (ms) | share | DRAM bytes per launch |")
@@ -363,8 +368,13 @@ def max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
+GRID_OVERRIDE = None   # --n: profiling runs of an RT workload on a smaller grid
+
+
 def build_workload(cfg):
-    c = CONFIGS[cfg]
+    c = dict(CONFIGS[cfg])
+    if GRID_OVERRIDE is not None and c.get("kind", "rt") == "rt" and "n" in c:
+        c["n"] = GRID_OVERRIDE
     if c.get("batch") or c.get("served"):
         raise ValueError("batch and served configs have no single workload")
     kind = c.get("kind", "rt")
@@ -999,11 +1009,18 @@ def main():
                     help="FP32 vs FP64 Rayleigh-Taylor density error at t_end (no JSON bench line)")
     ap.add_argument("--precision-n", type=int, default=512)
     ap.add_argument("--t-end", type=float, default=0.5)
+    ap.add_argument("--traffic-scale", type=float, default=1.0,
+                    help="with --record-traffic: scale the captured bytes to the workload's cells")
+    ap.add_argument("--traffic-note", default="", help="with --record-traffic: how the capture was scaled")
+    ap.add_argument("--n", type=int, default=None,
+                    help="Rayleigh-Taylor configs: grid n^3 instead of the workload's (profiling a smaller case)")
     ap.add_argument("--record-traffic", metavar="NCU_CSV", default=None,
                     help="store DRAM bytes per launch from an ncu CSV of --config into profiles/traffic.json")
     args = ap.parse_args()
+    global GRID_OVERRIDE
+    GRID_OVERRIDE = args.n
     if args.record_traffic:
-        return record_traffic(args.config, args.record_traffic)
+        return record_traffic(args.config, args.record_traffic, args.traffic_scale, args.traffic_note)
     if args.precision_report:
         return run_precision_report(args)
     if args.warmup < 3:

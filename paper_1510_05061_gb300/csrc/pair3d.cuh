@@ -22,7 +22,7 @@
 
 namespace hydro {
 
-template <bool HSE, int TXP, int TY>
+template <bool HSE, int TXP, int TY, int MINB = 1>
 struct Pair3DSmem {
     static constexpr int NV = 5, H = 2;
     static constexpr int TX = 2 * TXP;          // cells per tile row
@@ -37,18 +37,20 @@ struct Pair3DSmem {
     static constexpr size_t plane = (size_t)NV * HY * HXS;
     static constexpr size_t rest = 2 * wx + 2 * wy + fx + fy;
     // a spare ring slot (staging the next plane in the half step's barrier
-    // interval) where shared memory allows
-    static constexpr bool spare = (4 * plane + rest) * 4 <= 226 * 1024;
+    // interval) where shared memory allows it for MINB resident CTAs (each
+    // with about 1.5 KB of reserved and static shared memory)
+    static constexpr bool spare = (4 * plane + rest) * 4 <= 226 * 1024 &&
+                                  MINB * ((4 * plane + rest) * 4 + 1536) <= 228 * 1024;
     static constexpr int NR = spare ? 4 : 3;
     static constexpr size_t bytes = (NR * plane + rest) * 4;
     static_assert(bytes <= 226 * 1024, "shared memory of one CTA");
 };
 
-template <bool HSE, int TXP, int TY, bool GZ>
+template <bool HSE, int TXP, int TY, bool GZ, int MINB>
 __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chunk, double dtd,
                                             unsigned char *smem_raw, float &smax, bool &bad)
 {
-    using S = Pair3DSmem<HSE, TXP, TY>;
+    using S = Pair3DSmem<HSE, TXP, TY, MINB>;
     constexpr int NV = 5, H = 2, NT = TXP * TY;
     constexpr int TX = S::TX, HX = S::HX, HY = S::HY, HXS = S::HXS, NR = S::NR;
     constexpr int WXS = S::WXS, FXS = S::FXS;
@@ -203,30 +205,17 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
         if constexpr (!MERGED) __syncthreads();
         const bool xy = (p >= z0 && p < z1);
         const bool fin = p > z0 && (own0 || own1);
-        f2 ufin[NV];
-        float bgB = 0.0f, bgR = 0.0f, bgP = 0.0f;
-        if (fin) {
-            const long long c = (long long)(p - 1) * plane + own_off;
-#pragma unroll
-            for (int q = 0; q < NV; ++q)
-                ufin[q] = pr(own0 ? U[c + q * vs] : 0.0f, own1 ? U[c + 1 + q * vs] : 0.0f);
-            if constexpr (HSE) {
-                bgB = bgT[p + 1].B;
-                bgR = bgT[p + 1].rho_c;
-                bgP = bgT[p + 1].p_c;
-            }
-        }
+        const bool wall_zlo = p == 0 && a.bc_lo[2] == BC_REFLECT;
+        const bool wall_zhi = p == nz && a.bc_hi[2] == BC_REFLECT;
 
-        // ---- step 2: half step of the own pair (z faces kept in registers)
-        f2 zlo[NV], ztop[NV];
+        // ---- step 2: half step of the own pair; its z faces stay in
+        // registers and the z flux below plane p is solved right away (it
+        // needs no other thread's states), which ends the low z states'
+        // lifetime before the x and y solves
+        f2 ztop[NV], fz[NV];
         {
             f2 w[NV], dw[3][NV], wh[NV];
             predict_pair(cx0, ty, p, w, dw, wh);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                zlo[q] = fma2(mhalf, dw[2][q], wh[q]);
-                ztop[q] = fma2(phalf, dw[2][q], wh[q]);
-            }
             if (xy) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
@@ -235,6 +224,27 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
                     WY2(wyl, q, ty, cx0) = fma2(mhalf, dw[1][q], wh[q]);
                     WY2(wyh, q, ty, cx0) = fma2(phalf, dw[1][q], wh[q]);
                 }
+            }
+            f2 zlo[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                zlo[q] = fma2(mhalf, dw[2][q], wh[q]);
+                ztop[q] = fma2(phalf, dw[2][q], wh[q]);
+            }
+            if (p >= z0) {
+                f2 wlz[NV], wrz[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    const f2 sg = bc(q == 3 ? -1.0f : 1.0f);
+                    wlz[q] = wall_zlo ? mul2(sg, zlo[q]) : ztop_prev[q];
+                    wrz[q] = wall_zhi ? mul2(sg, ztop_prev[q]) : zlo[q];
+                }
+                const float rb_f = HSE ? bgT[p + 2].rho_f : 0.0f;
+                const float pb_f = HSE ? bgT[p + 2].p_f : 0.0f;
+                hllc2<2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) fz[q] = bc(0.0f);
             }
         }
         if (xy) {
@@ -268,57 +278,59 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
         }
         __syncthreads();
 
-        // ---- step 3: the pair's two low x faces, two low y faces and two z
-        // faces below plane p (three packed solves), then the tile's
-        // high-side faces (x: the rows' faces TX two rows at a time on warp
-        // 0; y: aligned pairs of row TY on warp 1)
+        // ---- step 3: the pair's two low x faces, then its two low y faces
+        // (one packed solve each, in turn), then the tile's high-side faces
+        // (x: the rows' faces TX two rows at a time on warp 0; y: aligned
+        // pairs of row TY on warp 1)
         const float rb_c = HSE ? bgT[p + 2].rho_c : 0.0f;
         const float pb_c = HSE ? bgT[p + 2].p_c : 0.0f;
-        const float rb_f = HSE ? bgT[p + 2].rho_f : 0.0f;
-        const float pb_f = HSE ? bgT[p + 2].p_f : 0.0f;
-        const bool wall_zlo = p == 0 && a.bc_lo[2] == BC_REFLECT;
-        const bool wall_zhi = p == nz && a.bc_hi[2] == BC_REFLECT;
-        f2 fz[NV];
         if (xy) {
-            f2 wlx[NV], wrx[NV], wly[NV], wry[NV], wlz[NV], wrz[NV], fxv[NV], fyv[NV];
             const bool wall_tile = (a.bc_lo[0] == BC_REFLECT && x0 == 0) || (a.bc_hi[0] == BC_REFLECT && x0 + TX >= nx)
-                                || (a.bc_lo[1] == BC_REFLECT && y0 == 0) || (a.bc_hi[1] == BC_REFLECT && y0 + TY >= ny)
-                                || wall_zlo || wall_zhi;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const f2 own_xh = WX2(wxh, q, ty, cx0);
-                wlx[q] = pr(WX(wxh, q, ty, cx0 - 1), own_xh.x);
-                wrx[q] = WX2(wxl, q, ty, cx0);
-                wly[q] = WY2(wyh, q, ty - 1, cx0);
-                wry[q] = WY2(wyl, q, ty, cx0);
-                wlz[q] = ztop_prev[q];
-                wrz[q] = zlo[q];
-            }
-            if (wall_tile) {
-                // a reflecting wall replaces the far-side state by the mirror
-                // image of the near side's, per lane
-                const bool xlo0 = gx == 0 && a.bc_lo[0] == BC_REFLECT, xlo1 = gx + 1 == 0 && a.bc_lo[0] == BC_REFLECT;
-                const bool xhi0 = gx == nx && a.bc_hi[0] == BC_REFLECT, xhi1 = gx + 1 == nx && a.bc_hi[0] == BC_REFLECT;
-                const bool ylo = gy == 0 && a.bc_lo[1] == BC_REFLECT, yhi = gy == ny && a.bc_hi[1] == BC_REFLECT;
+                                || (a.bc_lo[1] == BC_REFLECT && y0 == 0) || (a.bc_hi[1] == BC_REFLECT && y0 + TY >= ny);
+            {
+                f2 wl[NV], wr[NV], f[NV];
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    const float sx = q == 1 ? -1.0f : 1.0f, sy = q == 2 ? -1.0f : 1.0f, sz = q == 3 ? -1.0f : 1.0f;
-                    const f2 xl = wlx[q], xr = wrx[q], yl = wly[q], yr = wry[q], zl = wlz[q], zr = wrz[q];
-                    wlx[q] = pr(xlo0 ? sx * xr.x : xl.x, xlo1 ? sx * xr.y : xl.y);
-                    wrx[q] = pr(xhi0 ? sx * xl.x : xr.x, xhi1 ? sx * xl.y : xr.y);
-                    wly[q] = ylo ? mul2(bc(sy), yr) : yl;
-                    wry[q] = yhi ? mul2(bc(sy), yl) : yr;
-                    wlz[q] = wall_zlo ? mul2(bc(sz), zr) : zl;
-                    wrz[q] = wall_zhi ? mul2(bc(sz), zl) : zr;
+                    wl[q] = pr(WX(wxh, q, ty, cx0 - 1), WX(wxh, q, ty, cx0));
+                    wr[q] = WX2(wxl, q, ty, cx0);
                 }
-            }
-            hllc2<0, HSE>(wlx, wrx, rb_c, pb_c, gam, igm1, fxv);
-            hllc2<1, HSE>(wly, wry, rb_c, pb_c, gam, igm1, fyv);
-            hllc2<2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
+                if (wall_tile) {
+                    // a reflecting wall replaces the far-side state by the
+                    // mirror image of the near side's, per lane
+                    const bool lo0 = gx == 0 && a.bc_lo[0] == BC_REFLECT, lo1 = gx + 1 == 0 && a.bc_lo[0] == BC_REFLECT;
+                    const bool hi0 = gx == nx && a.bc_hi[0] == BC_REFLECT, hi1 = gx + 1 == nx && a.bc_hi[0] == BC_REFLECT;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                FX2(q, ty, cx0) = fxv[q];
-                FY2(q, ty, cx0) = fyv[q];
+                    for (int q = 0; q < NV; ++q) {
+                        const float sx = q == 1 ? -1.0f : 1.0f;
+                        const f2 l = wl[q], r = wr[q];
+                        wl[q] = pr(lo0 ? sx * r.x : l.x, lo1 ? sx * r.y : l.y);
+                        wr[q] = pr(hi0 ? sx * l.x : r.x, hi1 ? sx * l.y : r.y);
+                    }
+                }
+                hllc2<0, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) FX2(q, ty, cx0) = f[q];
+            }
+            {
+                f2 wl[NV], wr[NV], f[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    wl[q] = WY2(wyh, q, ty - 1, cx0);
+                    wr[q] = WY2(wyl, q, ty, cx0);
+                }
+                if (wall_tile) {
+                    const bool lo = gy == 0 && a.bc_lo[1] == BC_REFLECT, hi = gy == ny && a.bc_hi[1] == BC_REFLECT;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        const f2 sy = bc(q == 2 ? -1.0f : 1.0f);
+                        const f2 l = wl[q], r = wr[q];
+                        wl[q] = lo ? mul2(sy, r) : l;
+                        wr[q] = hi ? mul2(sy, l) : r;
+                    }
+                }
+                hllc2<1, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) FY2(q, ty, cx0) = f[q];
             }
             if (tid < TY / 2 || (tid >= 32 && tid < 32 + TXP)) {
                 f2 wl[NV], wr[NV], f[NV];
@@ -350,18 +362,6 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
                     for (int q = 0; q < NV; ++q) FY2(q, TY, cx) = f[q];
                 }
             }
-        } else if (p == z1) {
-            f2 wlz[NV], wrz[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const f2 s = bc(q == 3 ? -1.0f : 1.0f);
-                wlz[q] = wall_zlo ? mul2(s, zlo[q]) : ztop_prev[q];
-                wrz[q] = wall_zhi ? mul2(s, ztop_prev[q]) : zlo[q];
-            }
-            hllc2<2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
-        } else {
-#pragma unroll
-            for (int q = 0; q < NV; ++q) fz[q] = bc(0.0f);
         }
         __syncthreads();
 
@@ -370,7 +370,10 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
             const long long c = (long long)(p - 1) * plane + own_off;
             f2 u[NV], du[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) u[q] = ufin[q];
+            for (int q = 0; q < NV; ++q) u[q] = pr(own0 ? U[c + q * vs] : 0.0f, own1 ? U[c + 1 + q * vs] : 0.0f);
+            const float bgB = HSE ? bgT[p + 1].B : 0.0f;
+            const float bgR = HSE ? bgT[p + 1].rho_c : 0.0f;
+            const float bgP = HSE ? bgT[p + 1].p_c : 0.0f;
             const f2 idz = bc(inv_dx[2]);
 #pragma unroll
             for (int q = 0; q < NV; ++q) du[q] = mul2(bc(-1.0f), fma2(sub2(fz[q], fz_prev[q]), idz, div_prev[q]));
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(TXP * TY, MINB) step3d_pair_kernel(const StepA
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     float smax;
     bool bad;
-    pair3d_body<HSE, TXP, TY, GZ>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    pair3d_body<HSE, TXP, TY, GZ, MINB>(a, tile, chunk, dtd, smem_raw, smax, bad);
     const bool bad_cta = __syncthreads_or(bad) != 0;
     const double m = block_max_t<NT, float>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd, true,

@@ -13,7 +13,7 @@ template <bool HSE, int TXP, int TY, int MINB, bool GZ>
 cudaError_t launch_pair(const StepArgs &a, dim3 grid, cudaStream_t s)
 {
     auto k = step3d_pair_kernel<HSE, TXP, TY, GZ, MINB>;
-    constexpr size_t smem = Pair3DSmem<HSE, TXP, TY>::bytes;
+    constexpr size_t smem = Pair3DSmem<HSE, TXP, TY, MINB>::bytes;
     static PerDeviceOnce configured;   // the attribute is per function and device
     const cudaError_t e = ensure_smem_limit(configured, k, smem);
     if (e != cudaSuccess) return e;
@@ -35,7 +35,7 @@ cudaError_t launch_v(int pv, const StepArgs &a, dim3 grid, cudaStream_t s)
 {
     switch (pv) {
     // (threads x, threads y, CTAs per SM asked of the register allocation)
-    case 0: return launch_g<HSE, 16, 16, 1>(a, grid, s);   // 32 x 16 cells, 256 threads, 1 CTA per SM
+    case 0: return launch_g<HSE, 16, 16, 2>(a, grid, s);   // 32 x 16 cells, 256 threads, 2 CTAs per SM
     case 1: return launch_g<HSE, 16, 8, 3>(a, grid, s);    // 32 x 8 cells, 128 threads, 3 CTAs per SM
     case 2: return launch_g<HSE, 8, 16, 3>(a, grid, s);    // 16 x 16 cells, 128 threads, 3 CTAs per SM
     default: return cudaErrorInvalidValue;
