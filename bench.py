@@ -144,17 +144,53 @@ def step_kernel_names(prob, variant: int):
              if prob.ndim == 3 else f"step2d_kernel<{tname}, 32, 8, {st}, {prob.recon}>") for st in stages]
 
 
-def kernel_source_sha() -> str:
-    """Hash of the CUDA sources: measured traffic is valid only for the
-    kernels it was taken from."""
+# translation units that compile (and launch) each kernel family; a kernel's
+# source hash covers them and every csrc header they include
+KERNEL_UNITS = {
+    "step3d_kernel": ("step3d_f64.cu", "step3d_f32.cu", "stage3d_f64.cu", "stage3d_f32.cu"),
+    "step3d_pair_kernel": ("pair3d_f32.cu",),
+    "step3d_batch_kernel": ("batch3d_f64.cu", "batch3d_f32.cu"),
+    "step2d_kernel": ("step2d.cu",),
+    "step2d_batch_kernel": ("batch2d.cu",),
+    "ctu3d_kernel": ("ctu3d.cu",),
+    "ctu2d_kernel": ("ctu2d.cu",),
+}
+
+
+def _csrc_closure(units):
+    """The units and every csrc file they include, transitively."""
+    import re
+
+    csrc = os.path.join(ROOT, "paper_1510_05061_gb300", "csrc")
+    seen, todo = set(), list(units)
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += [m for m in re.findall(r'#include\s+"([^"/]+)"', fh.read())]
+    return sorted(seen)
+
+
+def kernel_source_sha(kernel: str = "") -> str:
+    """Hash of the CUDA sources a kernel is built from (its family's
+    translation units and the csrc headers they include; every source when
+    the kernel is not known): measured traffic is valid only for the
+    sources it was taken from."""
     import glob
     import hashlib
 
+    csrc = os.path.join(ROOT, "paper_1510_05061_gb300", "csrc")
+    family = kernel.split("<")[0].strip()
+    if family in KERNEL_UNITS:
+        files = [os.path.join(csrc, f) for f in _csrc_closure(KERNEL_UNITS[family])]
+    else:
+        files = [f for f in sorted(glob.glob(os.path.join(csrc, "*"))) if f.endswith((".cu", ".cuh", ".h"))]
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1510_05061_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(f, "rb") as fh:
-                h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
     return h.hexdigest()
 
 
@@ -168,7 +204,7 @@ def measured_traffic(config: str, kernel: str):
     except (OSError, ValueError):
         return None
     e = table.get(config, {}).get(kernel)
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return float(e["bytes_per_launch"])
 
@@ -200,9 +236,9 @@ def record_traffic(config: str, csv_path: str, scale: float = 1.0, note: str = "
             table = json.load(fh)
     except (OSError, ValueError):
         table = {}
-    sha = kernel_source_sha()
     # entries of this workload taken from other sources are stale: drop them
-    table[config] = {k: v for k, v in table.get(config, {}).items() if v.get("source_sha") == sha}
+    table[config] = {k: v for k, v in table.get(config, {}).items()
+                     if v.get("source_sha") == kernel_source_sha(k)}
     rows = []
     total_ns = 0.0
     for name, launches in per.items():
@@ -210,7 +246,8 @@ def record_traffic(config: str, csv_path: str, scale: float = 1.0, note: str = "
         byts = [m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0) for m in launches.values()]
         rows.append((name, len(launches), ns, sum(byts) / len(byts)))
         total_ns += ns
-        entry = {"bytes_per_launch": scale * sum(byts) / len(byts), "launches": len(launches), "source_sha": sha}
+        entry = {"bytes_per_launch": scale * sum(byts) / len(byts), "launches": len(launches),
+                 "source_sha": kernel_source_sha(name)}
         if scale != 1.0:
             entry["scaled"] = note or f"captured on a smaller grid, bytes x {scale:g}"
         table.setdefault(config, {})[name] = entry

@@ -57,13 +57,14 @@ def test_recorded_traffic_keys_are_names_bench_derives():
         for k, e in kernels.items():
             if k.startswith(("step3d_kernel", "ctu3d_kernel")):
                 entries.append((cfg, k, e.get("source_sha")))
-    shas = collections.Counter(sha for _, _, sha in entries)
-    current = bench.kernel_source_sha()
-    latest = current if current in shas else shas.most_common(1)[0][0]
+    current = [(cfg, k, sha) for cfg, k, sha in entries if sha == bench.kernel_source_sha(k)]
+    if len(current) >= 8:
+        entries = current
+    else:    # the sources moved on since the capture: check the latest capture's names
+        latest = collections.Counter(sha for _, _, sha in entries).most_common(1)[0][0]
+        entries = [e for e in entries if e[2] == latest]
     checked = 0
     for cfg, k, sha in entries:
-        if sha != latest:
-            continue
         derived = {n for v in range(8) for n in bench.step_kernel_names(small(cfg), v)}
         assert k in derived, (cfg, k)
         checked += 1
@@ -85,3 +86,15 @@ def test_profile_commands_name_existing_workloads():
     assert names, "no workload named in the profiles"
     missing = sorted(n for n in names if n not in bench.CONFIGS)
     assert not missing, missing
+
+
+def test_source_hash_follows_a_kernels_own_sources():
+    """A kernel's traffic stays valid when only other kernels' sources change:
+    its hash covers its translation units and the headers they include."""
+    files = bench._csrc_closure(bench.KERNEL_UNITS["step3d_kernel"])
+    assert "step3d.cuh" in files and "hydro_device.cuh" in files and "hydro_internal.h" in files
+    assert "pair3d.cuh" not in files and "ctu3d.cuh" not in files
+    pair = bench._csrc_closure(bench.KERNEL_UNITS["step3d_pair_kernel"])
+    assert "pair_math.cuh" in pair and "step3d.cuh" in pair
+    assert bench.kernel_source_sha("step3d_kernel<double, 0, 16, 16, 0, 0, 1, 1>") != \
+        bench.kernel_source_sha("ctu3d_kernel<double, 0, 16, 8>")
