@@ -150,12 +150,14 @@ struct hydro_batch {
     BatchQueue *d_queue;
     BatchInst *d_insts;
     BatchItem *d_items3, *d_items2;
-    // pinned host staging of the uploads; rewritten only after the previous
-    // upload from it has completed (event `staged`)
-    unsigned char *pinned;
-    size_t pinned_bytes;
-    cudaEvent_t staged;
-    bool staged_pending;
+    // two pinned host staging buffers used in turn for the uploads; one is
+    // rewritten only after the upload made from it has completed (its event
+    // `staged`), i.e. the host waits at most for the upload before the last
+    unsigned char *pinned[2];
+    size_t pinned_bytes[2];
+    cudaEvent_t staged[2];
+    bool staged_pending[2];
+    int stage_buf;             // buffer the next upload uses
     int nitems3, nitems2, grid3, grid2;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -198,21 +200,22 @@ int zchunk_of(const hydro_batch *b, const hydro_problem &p)
     return (p.n[2] + nch - 1) / nch;
 }
 
-int ensure_pinned(hydro_batch *b, size_t need)
+// Staging buffer k ready for rewriting and holding at least `need` bytes.
+int ensure_pinned(hydro_batch *b, int k, size_t need)
 {
-    if (need <= b->pinned_bytes) return HYDRO_OK;
-    if (b->staged_pending && cudaEventSynchronize(b->staged) != cudaSuccess) return HYDRO_ERR_CUDA;
-    b->staged_pending = false;
-    if (b->pinned) cudaFreeHost(b->pinned);
-    b->pinned = nullptr;
-    b->pinned_bytes = 0;
+    if (b->staged_pending[k] && cudaEventSynchronize(b->staged[k]) != cudaSuccess) return HYDRO_ERR_CUDA;
+    b->staged_pending[k] = false;
+    if (need <= b->pinned_bytes[k]) return HYDRO_OK;
+    if (b->pinned[k]) cudaFreeHost(b->pinned[k]);
+    b->pinned[k] = nullptr;
+    b->pinned_bytes[k] = 0;
     size_t cap = 1 << 20;
     while (cap < need) cap *= 2;
-    if (cudaHostAlloc(reinterpret_cast<void **>(&b->pinned), cap, cudaHostAllocDefault) != cudaSuccess) {
-        b->pinned = nullptr;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&b->pinned[k]), cap, cudaHostAllocDefault) != cudaSuccess) {
+        b->pinned[k] = nullptr;
         return HYDRO_ERR_OOM;
     }
-    b->pinned_bytes = cap;
+    b->pinned_bytes[k] = cap;
     return HYDRO_OK;
 }
 
@@ -293,27 +296,29 @@ int rebuild(hydro_batch *b)
     const size_t i2_bytes = sizeof(BatchItem) * items2.size();
     const size_t q_bytes = offsetof(BatchQueue, next);   // list pointers and lengths, not the counters
     const size_t o_i3 = align_up(bi_bytes), o_i2 = o_i3 + align_up(i3_bytes), o_q = o_i2 + align_up(i2_bytes);
-    int rc = ensure_pinned(b, o_q + align_up(q_bytes));
+    const int k = b->stage_buf;
+    int rc = ensure_pinned(b, k, o_q + align_up(q_bytes));
     if (rc) return rc;
-    if (b->staged_pending && cudaEventSynchronize(b->staged) != cudaSuccess) return HYDRO_ERR_CUDA;
-    std::memcpy(b->pinned, insts.data(), bi_bytes);
-    if (i3_bytes) std::memcpy(b->pinned + o_i3, sorted3.data(), i3_bytes);
-    if (i2_bytes) std::memcpy(b->pinned + o_i2, items2.data(), i2_bytes);
+    unsigned char *pin = b->pinned[k];
+    std::memcpy(pin, insts.data(), bi_bytes);
+    if (i3_bytes) std::memcpy(pin + o_i3, sorted3.data(), i3_bytes);
+    if (i2_bytes) std::memcpy(pin + o_i2, items2.data(), i2_bytes);
     BatchQueue qh{};
     qh.items[0] = b->d_items3;
     qh.items[1] = b->d_items2;
     qh.nitems[0] = b->nitems3;
     qh.nitems[1] = b->nitems2;
-    std::memcpy(b->pinned + o_q, &qh, q_bytes);
-    cudaError_t e = cudaMemcpyAsync(b->d_insts, b->pinned, bi_bytes, cudaMemcpyHostToDevice, b->stream);
+    std::memcpy(pin + o_q, &qh, q_bytes);
+    cudaError_t e = cudaMemcpyAsync(b->d_insts, pin, bi_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && i3_bytes)
-        e = cudaMemcpyAsync(b->d_items3, b->pinned + o_i3, i3_bytes, cudaMemcpyHostToDevice, b->stream);
+        e = cudaMemcpyAsync(b->d_items3, pin + o_i3, i3_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && i2_bytes)
-        e = cudaMemcpyAsync(b->d_items2, b->pinned + o_i2, i2_bytes, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_queue, b->pinned + o_q, q_bytes, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
+        e = cudaMemcpyAsync(b->d_items2, pin + o_i2, i2_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_queue, pin + o_q, q_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->staged[k], b->stream);
     if (e != cudaSuccess) return HYDRO_ERR_CUDA;
-    b->staged_pending = true;
+    b->staged_pending[k] = true;
+    b->stage_buf = 1 - k;
 
     // persistent grids: the resident CTAs (the claim loop balances the items)
     const bool fp32 = b->precision == HYDRO_FP32;
@@ -564,7 +569,8 @@ int hydro_batch_create(int max_instances, long max_items3d, long max_items2d, in
     b->graph_variant = -1;
     // the queue's claim counters start at zero (the kernels reset them after each launch)
     cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(BatchQueue), b->stream);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged[1], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete b;
         return HYDRO_ERR_CUDA;
@@ -811,8 +817,10 @@ int hydro_batch_destroy(hydro_batch *b)
     if (!b) return HYDRO_ERR_INVALID_ARG;
     cudaStreamSynchronize(b->stream);
     drop_graph(b);
-    if (b->staged) cudaEventDestroy(b->staged);
-    if (b->pinned) cudaFreeHost(b->pinned);
+    for (int k = 0; k < 2; ++k) {
+        if (b->staged[k]) cudaEventDestroy(b->staged[k]);
+        if (b->pinned[k]) cudaFreeHost(b->pinned[k]);
+    }
     delete b;
     return HYDRO_OK;
 }

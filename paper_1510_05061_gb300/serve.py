@@ -165,6 +165,7 @@ class Server:
         self.active: Dict[int, Request] = {}
         self._bufs: Dict[int, list] = {}
         self.launched = 0            # batched steps enqueued so far
+        self._pending_keep = []      # pinned and device copies of admitted fields, until the next mark
         self._marks = collections.deque()   # (event, launched, requests retired with it, keepalive)
         self._timing = []            # (start event, end event, zone-updates, bytes) per enqueued run
         self.ticks = 0
@@ -209,7 +210,7 @@ class Server:
             return False
         hydro._check(rc, "hydro_batch_add_async")
         # the pinned copy must outlive its transfer: released with the next mark
-        self._pending_keep = getattr(self, "_pending_keep", []) + [w_pin, w_dev]
+        self._pending_keep += [w_pin, w_dev]
         req.slot = sid.value
         req.admit = now
         req.first_launch = self.launched
@@ -240,8 +241,7 @@ class Server:
         self.launched += k
         self.ticks += k
         finished = [r for r in self.active.values() if r.first_launch + r.steps <= self.launched]
-        keep = list(getattr(self, "_pending_keep", []))
-        self._pending_keep = []
+        keep, self._pending_keep = self._pending_keep, []
         for req in finished:
             if keep_results(req):
                 dt = np.float32 if self.precision == inputs.FP32 else np.float64

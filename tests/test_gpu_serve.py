@@ -153,3 +153,33 @@ def test_server_loop_never_waits_for_the_whole_stream(env, monkeypatch):
     assert calls["n"] <= 1            # the statistics' final synchronisation only
     for r in reqs:
         assert np.array_equal(r.result, solo_state(hydro, r)), r.id
+
+
+def test_queue_survives_an_empty_list_between_launches(env):
+    """The claim counters of a list reset themselves at the end of every
+    launch, so a list may sit empty (its launches skipped) while the other
+    one runs, and fill again: a 3D solve that leaves, 2D steps with no 3D
+    instance, a new 3D solve -- each result equals its solo run."""
+    torch, hydro, serve = env
+    mk = lambda i, fam, n, steps: serve.make_payload(serve.Request(id=i, arrival=0.0, family=fam, n=n, steps=steps,
+                                                                   seed=151005063 + i))
+    a, b, c = mk(0, "rt3d", 20, 4), mk(1, "kh2d", 40, 15), mk(2, "rt3d", 18, 5)
+    srv = serve.Server(budget_bytes=1e12, max_active=4, max_items3d=200000, max_items2d=20000)
+    keep = lambda r: True
+    assert srv.try_admit(a, 0.0) and srv.try_admit(b, 0.0)
+    done = []
+    while a.id in {r.id for r in srv.active.values()}:
+        done += srv.advance(keep)
+    for _ in range(3):                      # 2D only: the 3D launches are skipped
+        done += srv.advance(keep)
+    assert all(r.prob.ndim == 2 for r in srv.active.values())
+    assert srv.try_admit(c, 0.0)
+    while srv.active:
+        done += srv.advance(keep)
+    done += srv.poll(block=True)
+    while srv._marks:
+        done += srv.poll(block=True)
+    srv.close()
+    assert {r.id for r in done} == {0, 1, 2}
+    for r in (a, b, c):
+        assert np.array_equal(r.result, solo_state(hydro, r)), r.id
