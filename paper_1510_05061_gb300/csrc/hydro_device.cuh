@@ -43,6 +43,44 @@ __device__ __forceinline__ int map_index(int g, int n, int bclo, int bchi, bool 
     return min(max(g, 0), n - 1);
 }
 
+// ---- Row vectors for the staging loads.  A haloed tile row whose x range
+// lies inside the grid is fetched as aligned vectors of W cells (16 bytes:
+// float4 / double2; or 8 bytes: float2) instead of one 4- or 8-byte load per
+// cell: vector k of the row covers the cells x0 - W + W k .. x0 - 1 + W k,
+// TX / W + 2 vectors in all, so the row's halo of depth 2 is covered (with
+// W = 4 also the two cells beyond it on each side, which lie in the same
+// 32-byte sectors as the halo cells).  Two adjacent cells -- a pair -- are
+// then written to shared memory as one 8- or 16-byte store.
+template <typename T, int W> struct RowVec;
+template <> struct RowVec<float, 4> { using V = float4; };
+template <> struct RowVec<float, 2> { using V = float2; };
+template <> struct RowVec<double, 2> { using V = double2; };
+
+template <typename T, int W>
+__device__ __forceinline__ T vec_lane(const typename RowVec<T, W>::V &v, int e)
+{
+    return reinterpret_cast<const T *>(&v)[e];   // e a compile-time constant: a register
+}
+
+template <typename T, int W>
+__device__ __forceinline__ typename RowVec<T, W>::V ld_vec(const T *p)
+{
+    return __ldg(reinterpret_cast<const typename RowVec<T, W>::V *>(p));
+}
+
+// Whether the rows of a tile starting at x0, TX cells wide, can be fetched
+// as vectors of W cells: the state's base and variable planes aligned to a
+// vector (nx a multiple of W, so every row is), and the vectors' x range
+// [x0 - W, x0 + TX + W) inside [0, nx) -- no x boundary mapping in the halo.
+template <typename T, int TX, int W>
+__device__ __forceinline__ bool rows_vectorisable(const void *U, int nx, long long vs, int x0)
+{
+    static_assert(TX % W == 0, "tile width a multiple of the vector width");
+    constexpr unsigned long long align = W * sizeof(T);
+    return (reinterpret_cast<unsigned long long>(U) & (align - 1)) == 0 && nx % W == 0 && vs % W == 0 &&
+           x0 >= W && x0 + TX + W <= nx;
+}
+
 // Reciprocal square root, quotient and reciprocal in the working precision.
 // FP64 uses CUDA's IEEE-accurate double routines; FP32 uses the SFU
 // approximations (rsqrtf, __fdividef: at most 2 ulp), well inside the FP32

@@ -42,6 +42,8 @@ struct Pair3DSmem {
     static constexpr bool spare = (4 * plane + rest) * 4 <= 226 * 1024 &&
                                   MINB * ((4 * plane + rest) * 4 + 1536) <= 228 * 1024;
     static constexpr int NR = spare ? 4 : 3;
+    // cells per staging row vector (16 bytes)
+    static constexpr int VW = 4;
     static constexpr size_t bytes = (NR * plane + rest) * 4;
     static_assert(bytes <= 226 * 1024, "shared memory of one CTA");
 };
@@ -99,26 +101,93 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
         return *reinterpret_cast<f2 *>(&fys[(q * (TY + 1) + fyi) * TX + cx]);
     };
 
-    // ---- staging of plane pz (as step3d_body's synchronous staging)
+    // ---- staging of plane pz (as step3d_body's synchronous staging): row
+    // vectors of W cells where the tile's x halo lies inside the grid (VEC,
+    // the same for the whole CTA), else one load per cell with boundary
+    // index mapping; the same primitives either way
     constexpr int NLOAD = (HX * HY + NT - 1) / NT;
     constexpr int HXY = HX * HY;
-    int xyoff[NLOAD];
+    constexpr int W = S::VW;
+    constexpr int NQ = TX / W + 2;
+    constexpr int NVEC = NQ * HY;
+    constexpr int NVL = (NVEC + NT - 1) / NT;
+    constexpr int NOFF = NLOAD > NVL ? NLOAD : NVL;
+    using VW_t = typename RowVec<float, W>::V;
+    const bool vec = rows_vectorisable<float, TX, W>(a.U, nx, vs, x0);
+    int xyoff[NOFF];
     unsigned flips = 0;
+    if (vec) {
 #pragma unroll
-    for (int j = 0; j < NLOAD; ++j) {
-        const int i = tid + j * NT;
-        const int hx = i % HX, hy = i / HX;
-        bool fx, fy;
-        const int gxm = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
-        const int gym = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
-        xyoff[j] = gym * nx + gxm;
-        flips |= (fx ? 1u : 0u) << (2 * j);
-        flips |= (fy ? 1u : 0u) << (2 * j + 1);
+        for (int j = 0; j < NVL; ++j) {
+            const int i = tid + j * NT;
+            const int k = i % NQ, hy = i / NQ;
+            bool fy = false;
+            const int gym = i < NVEC ? map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy) : 0;
+            xyoff[j] = gym * nx + x0 + W * (k - 1);
+            flips |= (fy ? 1u : 0u) << (2 * j + 1);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NLOAD; ++j) {
+            const int i = tid + j * NT;
+            const int hx = i % HX, hy = i / HX;
+            bool fx, fy;
+            const int gxm = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
+            const int gym = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
+            xyoff[j] = gym * nx + gxm;
+            flips |= (fx ? 1u : 0u) << (2 * j);
+            flips |= (fy ? 1u : 0u) << (2 * j + 1);
+        }
     }
+    auto convert = [&](const float (&v)[NV], bool fx, bool fy, bool fz, float rho_bg, float (&o)[NV]) {
+        const float r = v[0];
+        const float m0 = fx ? -v[1] : v[1];
+        const float m1 = fy ? -v[2] : v[2];
+        const float m2 = fz ? -v[3] : v[3];
+        const float rho = HSE ? rho_bg + r : r;
+        const float rinv = __fdividef(1.0f, rho);
+        o[0] = r;
+        o[1] = m0 * rinv;
+        o[2] = m1 * rinv;
+        o[3] = m2 * rinv;
+        o[4] = (gam - 1.0f) * (v[4] - 0.5f * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+    };
     auto stage = [&](int pz) {
         bool fz;
         const int gz = map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
         const float *Up = U + (long long)gz * plane;
+        const int slot = (pz + 2 * NR) % NR;
+        const float rho_bg = HSE ? bgT[pz + 2].rho_c : 0.0f;
+        if (vec) {
+#pragma unroll
+            for (int j = 0; j < NVL; ++j) {
+                const int i = tid + j * NT;
+                if (i < NVEC) {
+                    const int k = i % NQ, hy = i / NQ;
+                    const bool fy = (flips >> (2 * j + 1)) & 1u;
+                    VW_t rv[NV];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) rv[q] = ld_vec<float, W>(Up + xyoff[j] + q * vs);
+#pragma unroll
+                    for (int e = 0; e < W; e += 2) {
+                        const int hx = W * (k - 1) + H + e;   // even
+                        if (W == 2 || (hx >= 0 && hx < HX)) {
+                            float va[NV], vb[NV], oa[NV], ob[NV];
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) {
+                                va[q] = vec_lane<float, W>(rv[q], e);
+                                vb[q] = vec_lane<float, W>(rv[q], e + 1);
+                            }
+                            convert(va, false, fy, fz, rho_bg, oa);
+                            convert(vb, false, fy, fz, rho_bg, ob);
+#pragma unroll
+                            for (int q = 0; q < NV; ++q) P2(slot, q, hy, hx) = pr(oa[q], ob[q]);
+                        }
+                    }
+                }
+            }
+            return;
+        }
         float raw[NLOAD][NV];
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
@@ -128,24 +197,15 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
                 for (int q = 0; q < NV; ++q) raw[j][q] = Up[xyoff[j] + q * vs];
             }
         }
-        const int slot = (pz + 2 * NR) % NR;
-        const float rho_bg = HSE ? bgT[pz + 2].rho_c : 0.0f;
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
             const int i = tid + j * NT;
             if (i < HXY) {
                 const int hx = i % HX, hy = i / HX;
-                const float r = raw[j][0];
-                const float m0 = (flips >> (2 * j)) & 1u ? -raw[j][1] : raw[j][1];
-                const float m1 = (flips >> (2 * j + 1)) & 1u ? -raw[j][2] : raw[j][2];
-                const float m2 = fz ? -raw[j][3] : raw[j][3];
-                const float rho = HSE ? rho_bg + r : r;
-                const float rinv = __fdividef(1.0f, rho);
-                P(slot, 0, hy, hx) = r;
-                P(slot, 1, hy, hx) = m0 * rinv;
-                P(slot, 2, hy, hx) = m1 * rinv;
-                P(slot, 3, hy, hx) = m2 * rinv;
-                P(slot, 4, hy, hx) = (gam - 1.0f) * (raw[j][4] - 0.5f * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+                float o[NV];
+                convert(raw[j], (flips >> (2 * j)) & 1u, (flips >> (2 * j + 1)) & 1u, fz, rho_bg, o);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) P(slot, q, hy, hx) = o[q];
             }
         }
     };
@@ -197,6 +257,11 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
     const int gx = x0 + cx0, gy = y0 + ty;
     const bool own0 = gx < nx && gy < ny, own1 = gx + 1 < nx && gy < ny;
     const int own_off = gy * nx + gx;
+    // the own pair read and written as one 8-byte vector per variable (gx is
+    // even; with nx and the variable stride even and both buffers 8-byte
+    // aligned, so is every pair's offset)
+    const bool own_vec = own0 && own1 && nx % 2 == 0 && vs % 2 == 0 &&
+                         ((reinterpret_cast<unsigned long long>(U) | reinterpret_cast<unsigned long long>(Un)) & 7ull) == 0;
 
     for (int pz = z0 - H; pz <= z0 + LEAD - 2; ++pz) stage(pz);
     __syncthreads();
@@ -370,7 +435,9 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
             const long long c = (long long)(p - 1) * plane + own_off;
             f2 u[NV], du[NV];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) u[q] = pr(own0 ? U[c + q * vs] : 0.0f, own1 ? U[c + 1 + q * vs] : 0.0f);
+            for (int q = 0; q < NV; ++q)
+                u[q] = own_vec ? __ldg(reinterpret_cast<const f2 *>(U + c + q * vs))
+                               : pr(own0 ? U[c + q * vs] : 0.0f, own1 ? U[c + 1 + q * vs] : 0.0f);
             const float bgB = HSE ? bgT[p + 1].B : 0.0f;
             const float bgR = HSE ? bgT[p + 1].rho_c : 0.0f;
             const float bgP = HSE ? bgT[p + 1].p_c : 0.0f;
@@ -397,8 +464,12 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
             u[4] = fma2(h, add2(du[4], msrc), u[4]);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                if (own0) Un[c + q * vs] = u[q].x;
-                if (own1) Un[c + 1 + q * vs] = u[q].y;
+                if (own_vec) {
+                    *reinterpret_cast<f2 *>(Un + c + q * vs) = u[q];
+                } else {
+                    if (own0) Un[c + q * vs] = u[q].x;
+                    if (own1) Un[c + 1 + q * vs] = u[q].y;
+                }
             }
             // CFL signal speed and admissibility of the new states
             const f2 rho = HSE ? add2(bc(bgR), u[0]) : u[0];

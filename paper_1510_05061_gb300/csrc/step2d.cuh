@@ -75,23 +75,49 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     auto FX = [&](int q, int cy, int fxi) -> T & { return fxs[(q * TY + cy) * (TX + 1) + fxi]; };
     auto FY = [&](int q, int fyi, int cx) -> T & { return fys[(q * (TY + 1) + fyi) * TX + cx]; };
 
-    // ---- stage the haloed tile as primitives
-    for (int i = tid; i < HX * HY; i += NT) {
-        const int hx = i % HX, hy = i / HX;
-        bool fx, fy;
-        const int sx = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
-        const int sy = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
-        const int c = sy * nx + sx;   // a plane holds fewer than 2^31 cells
-        const T r = U[c];
-        T m0 = U[c + vs], m1 = U[c + 2 * vs];
-        const T e = U[c + 3 * vs];
-        if (fx) m0 = -m0;
-        if (fy) m1 = -m1;
+    // ---- stage the haloed tile as primitives: rows as vectors of W cells
+    // where the x halo lies inside the grid (row vector layout:
+    // hydro_device.cuh, rows_vectorisable), else one load per cell with
+    // boundary index mapping; the same primitives either way
+    auto convert = [&](T r, T m0, T m1, T e, int hy, int hx) {
         const T rinv = rcp_t(r);
         P(0, hy, hx) = r;
         P(1, hy, hx) = m0 * rinv;
         P(2, hy, hx) = m1 * rinv;
         P(3, hy, hx) = (gam - T(1)) * (e - T(0.5) * (m0 * m0 + m1 * m1) * rinv);
+    };
+    constexpr int W = 16 / sizeof(T);
+    constexpr int NQ = TX / W + 2;
+    using V = typename RowVec<T, W>::V;
+    if (H == 2 && rows_vectorisable<T, TX, W>(a.U, nx, vs, x0)) {
+        for (int i = tid; i < NQ * HY; i += NT) {
+            const int k = i % NQ, hy = i / NQ;
+            bool fy;
+            const int sy = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
+            const T *src = U + sy * nx + x0 + W * (k - 1);
+            V rv[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) rv[q] = ld_vec<T, W>(src + q * vs);
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const int hx = W * (k - 1) + H + e;
+                if (W == 2 || (hx >= 0 && hx < HX)) {
+                    const T m1 = vec_lane<T, W>(rv[2], e);
+                    convert(vec_lane<T, W>(rv[0], e), vec_lane<T, W>(rv[1], e), fy ? -m1 : m1,
+                            vec_lane<T, W>(rv[3], e), hy, hx);
+                }
+            }
+        }
+    } else {
+        for (int i = tid; i < HX * HY; i += NT) {
+            const int hx = i % HX, hy = i / HX;
+            bool fx, fy;
+            const int sx = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
+            const int sy = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
+            const int c = sy * nx + sx;   // a plane holds fewer than 2^31 cells
+            const T m0 = U[c + vs], m1 = U[c + 2 * vs];
+            convert(U[c], fx ? -m0 : m0, fy ? -m1 : m1, U[c + 3 * vs], hy, hx);
+        }
     }
     __syncthreads();
 

@@ -73,9 +73,18 @@ struct Step3DSmem {
     static constexpr size_t wy = (size_t)NV * (TY + 2) * TX;   // [NV][TY+2][TX]
     static constexpr size_t fx = (size_t)NV * TY * (TX + 1);   // [NV][TY][TX+1]
     static constexpr size_t fy = (size_t)NV * (TY + 1) * TX;   // [NV][TY+1][TX]
-    // conserved values of the next two planes as copied from HBM
+    // conserved values of the next two planes as copied from HBM, per
+    // variable either HY x HX mapped cells or HY rows of TX / W + 2 16-byte
+    // vectors (W cells each), whichever is larger, rounded to a vector
     static constexpr bool async = HYDRO_ASYNC_STAGING != 0 && AS;
-    static constexpr size_t raw = async ? 2ull * NV * HX * HY : 0;   // [2][NV][HY*HX]
+    static constexpr int ctas = HYDRO_STEP3D_MIN_CTAS(T, TX, TY);
+    // cells per row vector: 16 bytes, except the FP32 tiles held to 80
+    // registers (three CTAs per SM) with synchronous staging, whose four
+    // loaded vectors of 16 bytes would spill: 8 bytes there
+    static constexpr int VW = sizeof(T) == 8 ? 2 : (async || ctas < 3 ? 4 : 2);
+    static constexpr size_t rps0 = (size_t)HY * (HX > TX + 2 * VW ? HX : TX + 2 * VW);
+    static constexpr size_t rps = (rps0 + VW - 1) / VW * VW;
+    static constexpr size_t raw = async ? 2ull * NV * rps + VW : 0;   // [2][NV][rps], + alignment pad
     // planes the half step reads (p-1..p+1, PPM p-2..p+2), and one spare
     // slot where it fits: the next plane is then converted into the spare
     // slot in the same barrier interval as the half step (spare = true)
@@ -92,7 +101,6 @@ struct Step3DSmem {
     // for FP64 PPM; -5 % for the FP32 32 x 16 tile with asynchronous staging
     // and -0.4 % for the FP64 PLM tiles, which keep the plain ring.
     static constexpr size_t spare_bytes = ((NRS + 1) * plane + rest) * sizeof(T);
-    static constexpr int ctas = HYDRO_STEP3D_MIN_CTAS(T, TX, TY);
     static constexpr bool spare = spare_bytes <= 226 * 1024 && ctas * (spare_bytes + 1536) <= 228 * 1024
                                && (!async || (sizeof(T) == 8 && RC == RECON_PPM));
     static constexpr int NR = NRS + (spare ? 1 : 0);
@@ -111,6 +119,15 @@ __device__ __forceinline__ void cp_async_elem(T *smem_dst, const T *gmem_src)
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(sizeof(T))
                  : "memory");
+}
+// Asynchronous global->shared copy of N = 8 or 16 bytes (both addresses
+// aligned to N).
+template <int N>
+__device__ __forceinline__ void cp_async_vec(void *smem_dst, const void *gmem_src)
+{
+    static_assert(N == 8 || N == 16, "8- or 16-byte vectors");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(N) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -148,7 +165,8 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
     T *fxs = wyh + S::wy, *fys = fxs + S::fx;
-    T *rawbuf = fys + S::fy;
+    // (16-byte aligned: the vector copies land there)
+    T *rawbuf = reinterpret_cast<T *>((reinterpret_cast<unsigned long long>(fys + S::fy) + 15ull) & ~15ull);
 
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
@@ -186,73 +204,184 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     // primitives in shared memory, negating mirrored momenta.  With ASYNC
     // the loads are cp.async copies into a two-plane shared buffer, issued
     // one plane ahead; each thread converts exactly the elements it copied,
-    // so its own wait_group suffices.  The x-y mapping of a thread's
-    // elements is the same on every plane and is computed once.
+    // so its own wait_group suffices.  A tile whose x halo lies inside the
+    // grid (VEC, the same for the whole CTA) fetches its rows as 16-byte
+    // vectors (row vector layout: hydro_device.cuh, rows_vectorisable) and
+    // stores pairs of cells; the others take one load per cell.  Both give
+    // the same primitives (the same conversion of the same values).  The
+    // x-y mapping of a thread's elements is the same on every plane and is
+    // computed once.
     constexpr int NLOAD = (HX * HY + NT - 1) / NT;
     constexpr int HXY = HX * HY;
-    int xyoff[NLOAD];         // mapped in-plane offset of each element
+    constexpr int W = S::VW;                  // cells per vector
+    constexpr int NQ = TX / W + 2;            // vectors per row
+    constexpr int NVEC = NQ * HY;
+    constexpr int NVL = (NVEC + NT - 1) / NT;
+    constexpr int NOFF = NLOAD > NVL ? NLOAD : NVL;
+    constexpr int RPS = static_cast<int>(S::rps);
+    using V16 = typename RowVec<T, W>::V;
+    using P2 = typename RowVec<T, 2>::V;
+    static_assert(HXS % 2 == 0, "pairs of staged cells are 2-element aligned");
+    const bool vec = H == 2 && rows_vectorisable<T, TX, W>(a.U, nx, vs, x0);
+    int xyoff[NOFF];          // mapped in-plane offset of each element (or vector)
     unsigned flips = 0;       // bit 2j: x mirror, bit 2j+1: y mirror
+    if (vec) {
 #pragma unroll
-    for (int j = 0; j < NLOAD; ++j) {
-        const int i = tid + j * NT;
-        const int hx = i % HX, hy = i / HX;
-        bool fx, fy;
-        const int gxm = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
-        const int gym = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
-        xyoff[j] = gym * nx + gxm;
-        flips |= (fx ? 1u : 0u) << (2 * j);
-        flips |= (fy ? 1u : 0u) << (2 * j + 1);
+        for (int j = 0; j < NVL; ++j) {
+            const int i = tid + j * NT;
+            const int k = i % NQ, hy = i / NQ;
+            bool fy = false;
+            const int gym = i < NVEC ? map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy) : 0;
+            xyoff[j] = gym * nx + x0 + W * (k - 1);
+            flips |= (fy ? 1u : 0u) << (2 * j + 1);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NLOAD; ++j) {
+            const int i = tid + j * NT;
+            const int hx = i % HX, hy = i / HX;
+            bool fx, fy;
+            const int gxm = map_index(x0 + hx - H, nx, a.bc_lo[0], a.bc_hi[0], fx);
+            const int gym = map_index(y0 + hy - H, ny, a.bc_lo[1], a.bc_hi[1], fy);
+            xyoff[j] = gym * nx + gxm;
+            flips |= (fx ? 1u : 0u) << (2 * j);
+            flips |= (fy ? 1u : 0u) << (2 * j + 1);
+        }
     }
+    // conserved -> primitive of one cell (o[NV] = 1/rho where staged)
+    auto convert = [&](const T (&v)[NV], bool fx, bool fy, bool fz, T rho_bg, T (&o)[NVS]) {
+        const T r = v[0];
+        const T m0 = fx ? -v[1] : v[1];
+        const T m1 = fy ? -v[2] : v[2];
+        const T m2 = fz ? -v[3] : v[3];
+        const T rho = HSE ? rho_bg + r : r;
+        const T rinv = rcp_t(rho);
+        o[0] = r;
+        o[1] = m0 * rinv;
+        o[2] = m1 * rinv;
+        o[3] = m2 * rinv;
+        o[4] = (gam - T(1)) * (v[4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+        if constexpr (NVS > NV) o[NV] = rinv;
+    };
+    // the W cells of vector k of row hy, converted, as pairs (the two FP32
+    // cells beyond the halo at either end of the row are dropped)
+    auto put_vec = [&](int slot, int i, const V16 (&rv)[NV], bool fy, bool fz, T rho_bg) {
+        const int k = i % NQ, hy = i / NQ;
+#pragma unroll
+        for (int e = 0; e < W; e += 2) {
+            const int hx = W * (k - 1) + H + e;
+            if (W == 2 || (hx >= 0 && hx < HX)) {
+                T va[NV], vb[NV], oa[NVS], ob[NVS];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) { va[q] = vec_lane<T, W>(rv[q], e); vb[q] = vec_lane<T, W>(rv[q], e + 1); }
+                convert(va, false, fy, fz, rho_bg, oa);
+                convert(vb, false, fy, fz, rho_bg, ob);
+#pragma unroll
+                for (int q = 0; q < NVS; ++q) {
+                    P2 pr;
+                    pr.x = oa[q];
+                    pr.y = ob[q];
+                    *reinterpret_cast<P2 *>(&P(slot, q, hy, hx)) = pr;
+                }
+            }
+        }
+    };
     T raw[ASYNC ? 1 : NLOAD][NV];
     auto fetch = [&](int pz) {
         bool fz;
         const int gz = map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
         // gz is -2 or -1 below a halo side: signed plane offset
         const T *Up = U + (long long)gz * plane;
-        T *rb = rawbuf + ((pz + 4) & 1) * (NV * HXY);
+        T *rb = rawbuf + ((pz + 4) & 1) * (NV * RPS);
+        if constexpr (ASYNC) {
+            if (vec) {
 #pragma unroll
-        for (int j = 0; j < NLOAD; ++j) {
-            const int i = tid + j * NT;
-            if (i < HXY) {
-                const T *src = Up + xyoff[j];
-                if constexpr (ASYNC) {
+                for (int j = 0; j < NVL; ++j) {
+                    const int i = tid + j * NT;
+                    if (i < NVEC) {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) cp_async_elem(rb + q * HXY + i, src + q * vs);
-                } else {
+                        for (int q = 0; q < NV; ++q) cp_async_vec<W * sizeof(T)>(rb + q * RPS + i * W, Up + xyoff[j] + q * vs);
+                    }
+                }
+            } else {
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) raw[ASYNC ? 0 : j][q] = src[q * vs];
+                for (int j = 0; j < NLOAD; ++j) {
+                    const int i = tid + j * NT;
+                    if (i < HXY) {
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) cp_async_elem(rb + q * RPS + i, Up + xyoff[j] + q * vs);
+                    }
+                }
+            }
+            cp_async_commit();
+        } else {
+#pragma unroll
+            for (int j = 0; j < NLOAD; ++j) {
+                const int i = tid + j * NT;
+                if (i < HXY) {
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) raw[ASYNC ? 0 : j][q] = Up[xyoff[j] + q * vs];
                 }
             }
         }
-        if constexpr (ASYNC) cp_async_commit();
     };
     auto store = [&](int pz) {
         const int slot = (pz + 2 * NR) % NR;
         const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
         bool fz;
         map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
-        const T *rb = rawbuf + ((pz + 4) & 1) * (NV * HXY);
+        const T *rb = rawbuf + ((pz + 4) & 1) * (NV * RPS);
         if constexpr (ASYNC) cp_async_wait_all();
+        if (ASYNC && vec) {
+#pragma unroll
+            for (int j = 0; j < NVL; ++j) {
+                const int i = tid + j * NT;
+                if (i < NVEC) {
+                    V16 rv[NV];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) rv[q] = *reinterpret_cast<const V16 *>(rb + q * RPS + i * W);
+                    put_vec(slot, i, rv, (flips >> (2 * j + 1)) & 1u, fz, rho_bg);
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int j = 0; j < NLOAD; ++j) {
             const int i = tid + j * NT;
             if (i < HXY) {
                 const int hx = i % HX, hy = i / HX;
-                T v[NV];
+                T v[NV], o[NVS];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) v[q] = ASYNC ? rb[q * HXY + i] : raw[ASYNC ? 0 : j][q];
-                const T r = v[0];
-                const T m0 = (flips >> (2 * j)) & 1u ? -v[1] : v[1];
-                const T m1 = (flips >> (2 * j + 1)) & 1u ? -v[2] : v[2];
-                const T m2 = fz ? -v[3] : v[3];
-                const T rho = HSE ? rho_bg + r : r;
-                const T rinv = rcp_t(rho);
-                P(slot, 0, hy, hx) = r;
-                P(slot, 1, hy, hx) = m0 * rinv;
-                P(slot, 2, hy, hx) = m1 * rinv;
-                P(slot, 3, hy, hx) = m2 * rinv;
-                P(slot, 4, hy, hx) = (gam - T(1)) * (v[4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
-                if constexpr (NVS > NV) P(slot, NV, hy, hx) = rinv;
+                for (int q = 0; q < NV; ++q) v[q] = ASYNC ? rb[q * RPS + i] : raw[ASYNC ? 0 : j][q];
+                convert(v, (flips >> (2 * j)) & 1u, (flips >> (2 * j + 1)) & 1u, fz, rho_bg, o);
+#pragma unroll
+                for (int q = 0; q < NVS; ++q) P(slot, q, hy, hx) = o[q];
+            }
+        }
+    };
+    // synchronous staging: a vector tile loads and converts its vectors; the
+    // others fetch() and store()
+    auto stage_sync = [&](int pz) {
+        if (!vec) {
+            fetch(pz);
+            store(pz);
+            return;
+        }
+        bool fz;
+        const int gz = map_index<true>(pz, nz, a.bc_lo[2], a.bc_hi[2], fz);
+        const T *Up = U + (long long)gz * plane;
+        const int slot = (pz + 2 * NR) % NR;
+        const T rho_bg = HSE ? bgT[pz + 2].rho_c : T(0);
+        // (one vector's loads in flight at a time where a thread has several:
+        // their registers would spill)
+#pragma unroll
+        for (int j = 0; j < NVL; ++j) {
+            const int i = tid + j * NT;
+            if (i < NVEC) {
+                V16 rv[NV];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) rv[q] = ld_vec<T, W>(Up + xyoff[j] + q * vs);
+                put_vec(slot, i, rv, (flips >> (2 * j + 1)) & 1u, fz, rho_bg);
             }
         }
     };
@@ -340,8 +469,12 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
 
     // planes z0-H .. z0+LEAD-2 before the march; iteration p stages p+LEAD
     for (int pz = z0 - H; pz <= z0 + LEAD - 2; ++pz) {
-        fetch(pz);
-        store(pz);
+        if constexpr (ASYNC) {
+            fetch(pz);
+            store(pz);
+        } else {
+            stage_sync(pz);
+        }
     }
     __syncthreads();
     if constexpr (ASYNC) fetch(z0 + LEAD - 1);
@@ -367,8 +500,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             if (p + LEAD <= z1 + H - 1) store(p + LEAD);
             if (p + LEAD + 1 <= z1 + H - 1) fetch(p + LEAD + 1);
         } else if (p + LEAD <= z1 + H - 1) {
-            fetch(p + LEAD);
-            store(p + LEAD);
+            stage_sync(p + LEAD);
         }
         if constexpr (!MERGED) __syncthreads();
         const bool xy = (p >= z0 && p < z1);
