@@ -29,6 +29,26 @@ def cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "hydro_gb300", "autotune.json"))
 
 
+_LIB_TAG = None
+
+
+def lib_tag() -> str:
+    """Short content hash of the loaded libhydro.so: a rebuilt library (new
+    kernels) does not reuse choices timed on the old one."""
+    global _LIB_TAG
+    if _LIB_TAG is None:
+        import hashlib
+
+        from . import hydro
+
+        try:
+            with open(hydro.LIB_PATH, "rb") as fh:
+                _LIB_TAG = hashlib.sha1(fh.read()).hexdigest()[:12]
+        except OSError:
+            _LIB_TAG = "unknown"
+    return _LIB_TAG
+
+
 def signature(batch) -> str:
     import torch
 
@@ -40,7 +60,7 @@ def signature(batch) -> str:
     hse = int(any(p.hse_subtract for p in p3))
     mag = f"{cells:.2g}" if cells else "0"
     span = f"{ns[0]}-{ns[-1]}" if ns else "none"
-    return f"{torch.cuda.get_device_name()}|batch-v2|{prec}|hse{hse}|n3d={len(p3)}|cells={mag}|n={span}"
+    return f"{torch.cuda.get_device_name()}|batch-v2|lib={lib_tag()}|{prec}|hse{hse}|n3d={len(p3)}|cells={mag}|n={span}"
 
 
 def _load_cache() -> Dict[str, dict]:
@@ -123,7 +143,7 @@ def sim_signature(sim) -> str:
     scheme = {inputs.SSPRK2: "rk2", inputs.CTU: "ctu"}.get(getattr(p, "scheme", 0), "hancock")
     if getattr(p, "recon", 0) == inputs.PPM:
         scheme += "-ppm"
-    return (f"{torch.cuda.get_device_name()}|single-v2|{prec}|hse{p.hse_subtract}|{scheme}"
+    return (f"{torch.cuda.get_device_name()}|single-v2|lib={lib_tag()}|{prec}|hse{p.hse_subtract}|{scheme}"
             f"|n={p.n[0]}x{p.n[1]}x{p.n[2]}")
 
 

@@ -108,6 +108,27 @@ __device__ __forceinline__ float rcp_t(float b) { return __fdividef(1.0f, b); }
 __device__ __forceinline__ double div_t(double a, double b) { return a * rcp_t(b); }
 __device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
 
+// Conserved -> primitive pieces of the staging conversion with every
+// rounding spelled out (explicit multiplies and fused multiply-adds): the
+// compiler then has no contraction choices, so each staging path (row
+// vectors or mapped cells, in whichever kernel) gives the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// p = (gamma - 1)(E - |m|^2 / (2 rho)) from the momentum components m, the
+// total energy e, rinv = 1/rho and gm1 = gamma - 1: |m|^2 summed in axis
+// order, then (gamma - 1) fma(-1/2, |m|^2 / rho, E).
+template <typename T, int ND>
+__device__ __forceinline__ T pressure_of(const T (&m)[ND], T e, T rinv, T gm1)
+{
+    T k = mul_rn(m[0], m[0]);
+#pragma unroll
+    for (int d = 1; d < ND; ++d) k = fma_rn(m[d], m[d], k);
+    return mul_rn(gm1, fma_rn(T(-0.5), mul_rn(k, rinv), e));
+}
+
 // A step constant in the kernel's precision: the FP64 value, or its FP32
 // copy rounded on the host (the same value as a device-side conversion).
 template <typename T>

@@ -145,12 +145,13 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
         const float m1 = fy ? -v[2] : v[2];
         const float m2 = fz ? -v[3] : v[3];
         const float rho = HSE ? rho_bg + r : r;
-        const float rinv = __fdividef(1.0f, rho);
+        const float rinv = rcp_t(rho);
+        const float m[3] = {m0, m1, m2};
         o[0] = r;
-        o[1] = m0 * rinv;
-        o[2] = m1 * rinv;
-        o[3] = m2 * rinv;
-        o[4] = (gam - 1.0f) * (v[4] - 0.5f * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+        o[1] = mul_rn(m0, rinv);
+        o[2] = mul_rn(m1, rinv);
+        o[3] = mul_rn(m2, rinv);
+        o[4] = pressure_of<float, 3>(m, v[4], rinv, gam - 1.0f);
     };
     auto stage = [&](int pz) {
         bool fz;

@@ -81,10 +81,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     // boundary index mapping; the same primitives either way
     auto convert = [&](T r, T m0, T m1, T e, int hy, int hx) {
         const T rinv = rcp_t(r);
+        const T m[2] = {m0, m1};
         P(0, hy, hx) = r;
-        P(1, hy, hx) = m0 * rinv;
-        P(2, hy, hx) = m1 * rinv;
-        P(3, hy, hx) = (gam - T(1)) * (e - T(0.5) * (m0 * m0 + m1 * m1) * rinv);
+        P(1, hy, hx) = mul_rn(m0, rinv);
+        P(2, hy, hx) = mul_rn(m1, rinv);
+        P(3, hy, hx) = pressure_of<T, 2>(m, e, rinv, gam - T(1));
     };
     constexpr int W = 16 / sizeof(T);
     constexpr int NQ = TX / W + 2;

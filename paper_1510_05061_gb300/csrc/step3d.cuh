@@ -256,11 +256,12 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         const T m2 = fz ? -v[3] : v[3];
         const T rho = HSE ? rho_bg + r : r;
         const T rinv = rcp_t(rho);
+        const T m[3] = {m0, m1, m2};
         o[0] = r;
-        o[1] = m0 * rinv;
-        o[2] = m1 * rinv;
-        o[3] = m2 * rinv;
-        o[4] = (gam - T(1)) * (v[4] - T(0.5) * (m0 * m0 + m1 * m1 + m2 * m2) * rinv);
+        o[1] = mul_rn(m0, rinv);
+        o[2] = mul_rn(m1, rinv);
+        o[3] = mul_rn(m2, rinv);
+        o[4] = pressure_of<T, 3>(m, v[4], rinv, gam - T(1));
         if constexpr (NVS > NV) o[NV] = rinv;
     };
     // the W cells of vector k of row hy, converted, as pairs (the two FP32

@@ -77,6 +77,24 @@ def test_invalid_shapes_rejected(hy):
     assert hy.hydro_state_bytes(cp) == 0
 
 
+def test_plane_size_limit(hy):
+    """A z plane (nx * ny) is indexed with 32-bit offsets: 2^31 - 1 cells
+    is the largest accepted plane, and the byte counts of such a grid are
+    computed in 64 bits."""
+    from paper_1510_05061_gb300 import inputs
+
+    prob, _ = inputs.rayleigh_taylor(8, nz=4, perturb=False)
+    cp = hy.make_problem(prob)
+    cp.hse_subtract = 0
+    cp.n[0], cp.n[1], cp.n[2] = 65536, 32768, 2           # plane = 2^31
+    assert hy.hydro_state_bytes(cp) == 0
+    cp.n[0], cp.n[1], cp.n[2] = 46341, 46340, 2           # plane = 2147441940 < 2^31
+    assert hy.hydro_state_bytes(cp) == 5 * 46341 * 46340 * 2 * 8
+    cp.precision = 1
+    assert hy.hydro_state_bytes(cp) == 5 * 46341 * 46340 * 2 * 4
+    assert hy.hydro_workspace_bytes(cp) > 0
+
+
 def test_init_argument_errors_before_device(hy):
     from paper_1510_05061_gb300 import inputs
 
