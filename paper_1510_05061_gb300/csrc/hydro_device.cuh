@@ -239,22 +239,51 @@ __device__ __forceinline__ CellBG<T> cell_bg(const PlaneBGT<T> *bg, int k)
     return b;
 }
 
+// The face densities and pressures c -/+ dw_d / 2 of a cell (c: the cell's
+// half-step or centre state) into rp[d] = {rho_lo, rho_hi, p_lo, p_hi}, and
+// whether all of them are positive once the background is added back (HSE:
+// the face tables along z).  In plain mode the FP64 path skips the addition
+// of the zero background (0 + x is not folded for doubles); the FP32 path
+// keeps it (its measured instruction schedule).
+template <typename T, int ND, bool HSE>
+__device__ __forceinline__ bool face_rho_p_positive(const T (&c)[ND + 2], const T (&dw)[ND][ND + 2],
+                                                    const CellBG<T> &bg, T (&rp)[ND][4])
+{
+    constexpr int NV = ND + 2;
+    constexpr bool BGADD = HSE || sizeof(T) == 4;
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        T rb_lo = bg.rho, rb_hi = bg.rho, pb_lo = bg.p, pb_hi = bg.p;
+        if (HSE && d == 2) { rb_lo = bg.rho_lo; rb_hi = bg.rho_hi; pb_lo = bg.p_lo; pb_hi = bg.p_hi; }
+        rp[d][0] = c[0] - T(0.5) * dw[d][0];
+        rp[d][1] = c[0] + T(0.5) * dw[d][0];
+        rp[d][2] = c[NV - 1] - T(0.5) * dw[d][NV - 1];
+        rp[d][3] = c[NV - 1] + T(0.5) * dw[d][NV - 1];
+        const T r_lo = BGADD ? rb_lo + rp[d][0] : rp[d][0];
+        const T r_hi = BGADD ? rb_hi + rp[d][1] : rp[d][1];
+        const T p_lo = BGADD ? pb_lo + rp[d][2] : rp[d][2];
+        const T p_hi = BGADD ? pb_hi + rp[d][3] : rp[d][3];
+        ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
+    }
+    return ok;
+}
+
 // MUSCL-Hancock half step (Toro, 3rd ed., sec. 14.4) in primitive variables
 // for one cell: wh = w - (dt/2) sum_d A_d(w) dw_d / dx_d + (dt/2) S(w), where
 // S(w) is gravity on the velocities.  On return dw holds the slopes used
 // (all zero after the positivity fallback) and the face states are
-// wh -/+ dw_d / 2.  Returns true when the fallback was taken.
+// wh -/+ dw_d / 2; their densities and pressures, formed for the positivity
+// test, are returned in rp[d] = {rho_lo, rho_hi, p_lo, p_hi} (the same
+// values: the caller takes them instead of forming them again).  Returns
+// true when the fallback was taken.
 template <typename T, int ND, bool HSE, bool GZ = false, bool RINV = false>
 __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2],
-                                        T (&wh)[ND + 2], T hdt, const T (&inv_dx)[3],
+                                        T (&wh)[ND + 2], T (&rp)[ND][4], T hdt, const T (&inv_dx)[3],
                                         T gam, const T (&grav)[3], const CellBG<T> &bg,
                                         T rinv_given = T(0))
 {
     constexpr int NV = ND + 2;
-    // the background enters the positivity tests in HSE mode; in plain mode
-    // the FP64 path skips the addition of its zero (0 + x is not folded for
-    // doubles), the FP32 path keeps its measured instruction schedule
-    constexpr bool BGADD = HSE || sizeof(T) == 4;
     const T rho = HSE ? bg.rho + w[0] : w[0];
     const T pr = HSE ? bg.p + w[NV - 1] : w[NV - 1];
     // RINV: 1/rho as computed when the cell was staged (the same value)
@@ -299,17 +328,7 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     for (int q = 0; q < NV; ++q) wh[q] = w[q] + hdt * rate[q];
 
     // positivity of every predicted face density and pressure
-    bool ok = true;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        T rb_lo = bg.rho, rb_hi = bg.rho, pb_lo = bg.p, pb_hi = bg.p;
-        if (HSE && d == 2) { rb_lo = bg.rho_lo; rb_hi = bg.rho_hi; pb_lo = bg.p_lo; pb_hi = bg.p_hi; }
-        const T r_lo = BGADD ? rb_lo + (wh[0] - T(0.5) * dw[d][0]) : (wh[0] - T(0.5) * dw[d][0]);
-        const T r_hi = BGADD ? rb_hi + (wh[0] + T(0.5) * dw[d][0]) : (wh[0] + T(0.5) * dw[d][0]);
-        const T p_lo = BGADD ? pb_lo + (wh[NV - 1] - T(0.5) * dw[d][NV - 1]) : (wh[NV - 1] - T(0.5) * dw[d][NV - 1]);
-        const T p_hi = BGADD ? pb_hi + (wh[NV - 1] + T(0.5) * dw[d][NV - 1]) : (wh[NV - 1] + T(0.5) * dw[d][NV - 1]);
-        ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
-    }
+    const bool ok = face_rho_p_positive<T, ND, HSE>(wh, dw, bg, rp);
     if (!ok) {
 #pragma unroll
         for (int d = 0; d < ND; ++d)
@@ -320,37 +339,44 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
 #pragma unroll
         for (int d = 0; d < ND; ++d)
             if (!GZ || d == ND - 1) wh[1 + d] += hdt * gsrc[d];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            rp[d][0] = rp[d][1] = w[0];
+            rp[d][2] = rp[d][3] = w[NV - 1];
+        }
     }
     return !ok;
 }
 
+// Face state q of axis d (hi: the high face) of a cell after hancock or
+// mol_faces (there with wh = w): the density and pressure as returned in rp,
+// the velocities wh -/+ dw_d / 2.
+template <typename T, int ND>
+__device__ __forceinline__ T face_value(int q, int d, bool hi, const T (&wh)[ND + 2], const T (&dw)[ND][ND + 2],
+                                        const T (&rp)[ND][4])
+{
+    if (q == 0) return rp[d][hi ? 1 : 0];
+    if (q == ND + 1) return rp[d][hi ? 3 : 2];
+    return hi ? wh[q] + T(0.5) * dw[d][q] : wh[q] - T(0.5) * dw[d][q];
+}
+
 // Face states of the method of lines (no predictor): w -/+ dw_d / 2, with
 // the same positivity fallback as the half step (every slope of the cell
-// zeroed when a face density or pressure would not be positive).
+// zeroed when a face density or pressure would not be positive); rp as in
+// hancock.
 template <typename T, int ND, bool HSE>
-__device__ __forceinline__ void mol_faces(const T (&w)[ND + 2], T (&dw)[ND][ND + 2], const CellBG<T> &bg)
+__device__ __forceinline__ void mol_faces(const T (&w)[ND + 2], T (&dw)[ND][ND + 2], const CellBG<T> &bg,
+                                          T (&rp)[ND][4])
 {
     constexpr int NV = ND + 2;
-    // the background enters the positivity tests in HSE mode; in plain mode
-    // the FP64 path skips the addition of its zero (0 + x is not folded for
-    // doubles), the FP32 path keeps its measured instruction schedule
-    constexpr bool BGADD = HSE || sizeof(T) == 4;
-    bool ok = true;
+    if (!face_rho_p_positive<T, ND, HSE>(w, dw, bg, rp)) {
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        T rb_lo = bg.rho, rb_hi = bg.rho, pb_lo = bg.p, pb_hi = bg.p;
-        if (HSE && d == 2) { rb_lo = bg.rho_lo; rb_hi = bg.rho_hi; pb_lo = bg.p_lo; pb_hi = bg.p_hi; }
-        const T r_lo = BGADD ? rb_lo + (w[0] - T(0.5) * dw[d][0]) : (w[0] - T(0.5) * dw[d][0]);
-        const T r_hi = BGADD ? rb_hi + (w[0] + T(0.5) * dw[d][0]) : (w[0] + T(0.5) * dw[d][0]);
-        const T p_lo = BGADD ? pb_lo + (w[NV - 1] - T(0.5) * dw[d][NV - 1]) : (w[NV - 1] - T(0.5) * dw[d][NV - 1]);
-        const T p_hi = BGADD ? pb_hi + (w[NV - 1] + T(0.5) * dw[d][NV - 1]) : (w[NV - 1] + T(0.5) * dw[d][NV - 1]);
-        ok = ok && positive(r_lo) && positive(r_hi) && positive(p_lo) && positive(p_hi);
-    }
-    if (!ok) {
-#pragma unroll
-        for (int d = 0; d < ND; ++d)
+        for (int d = 0; d < ND; ++d) {
 #pragma unroll
             for (int q = 0; q < NV; ++q) dw[d][q] = T(0);
+            rp[d][0] = rp[d][1] = w[0];
+            rp[d][2] = rp[d][3] = w[NV - 1];
+        }
     }
 }
 

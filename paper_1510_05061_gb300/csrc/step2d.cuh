@@ -123,7 +123,7 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     __syncthreads();
 
     const CellBG<T> nobg = cell_bg<T, false>(static_cast<const PlaneBGT<T> *>(nullptr), 0);
-    auto predict = [&](int cx, int cy, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
+    auto predict = [&](int cx, int cy, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV], T (&rp)[ND][4]) {
         const int hx = cx + H, hy = cy + H;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -133,9 +133,9 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
             dw[1][q] = mc_slope(c - P(q, hy - 1, hx), P(q, hy + 1, hx) - c);
         }
         if constexpr (ST == STAGE_HANCOCK) {
-            hancock<T, ND, false>(w, dw, wh, hdt, inv_dx, gam, grav, nobg);
+            hancock<T, ND, false>(w, dw, wh, rp, hdt, inv_dx, gam, grav, nobg);
         } else {
-            mol_faces<T, ND, false>(w, dw, nobg);
+            mol_faces<T, ND, false>(w, dw, nobg, rp);
 #pragma unroll
             for (int q = 0; q < NV; ++q) wh[q] = w[q];
         }
@@ -166,14 +166,14 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
             WY(wyh, q, ty, tx) = hi;
         }
     } else {
-        T w[NV], dw[ND][NV], wh[NV];
-        predict(tx, ty, w, dw, wh);
+        T w[NV], dw[ND][NV], wh[NV], rp[ND][4];
+        predict(tx, ty, w, dw, wh, rp);
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            WX(wxl, q, ty, tx) = wh[q] - T(0.5) * dw[0][q];
-            WX(wxh, q, ty, tx) = wh[q] + T(0.5) * dw[0][q];
-            WY(wyl, q, ty, tx) = wh[q] - T(0.5) * dw[1][q];
-            WY(wyh, q, ty, tx) = wh[q] + T(0.5) * dw[1][q];
+            WX(wxl, q, ty, tx) = face_value<T, ND>(q, 0, false, wh, dw, rp);
+            WX(wxh, q, ty, tx) = face_value<T, ND>(q, 0, true, wh, dw, rp);
+            WY(wyl, q, ty, tx) = face_value<T, ND>(q, 1, false, wh, dw, rp);
+            WY(wyh, q, ty, tx) = face_value<T, ND>(q, 1, true, wh, dw, rp);
         }
     }
     constexpr int NRING = 2 * TY + 2 * TX;
@@ -197,23 +197,23 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
             }
             continue;
         }
-        T w[NV], dw[ND][NV], wh[NV];
-        predict(cx, cy, w, dw, wh);
+        T w[NV], dw[ND][NV], wh[NV], rp[ND][4];
+        predict(cx, cy, w, dw, wh, rp);
         if (xside) {
             if (cx < 0) {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) WX(wxh, q, cy, cx) = wh[q] + T(0.5) * dw[0][q];
+                for (int q = 0; q < NV; ++q) WX(wxh, q, cy, cx) = face_value<T, ND>(q, 0, true, wh, dw, rp);
             } else {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) WX(wxl, q, cy, cx) = wh[q] - T(0.5) * dw[0][q];
+                for (int q = 0; q < NV; ++q) WX(wxl, q, cy, cx) = face_value<T, ND>(q, 0, false, wh, dw, rp);
             }
         } else {
             if (cy < 0) {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) WY(wyh, q, cy, cx) = wh[q] + T(0.5) * dw[1][q];
+                for (int q = 0; q < NV; ++q) WY(wyh, q, cy, cx) = face_value<T, ND>(q, 1, true, wh, dw, rp);
             } else {
 #pragma unroll
-                for (int q = 0; q < NV; ++q) WY(wyl, q, cy, cx) = wh[q] - T(0.5) * dw[1][q];
+                for (int q = 0; q < NV; ++q) WY(wyl, q, cy, cx) = face_value<T, ND>(q, 1, false, wh, dw, rp);
             }
         }
     }

@@ -393,7 +393,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     // same operands, so the same bits) -- one FP64 subtraction and one
     // shared-memory load fewer per variable
     auto predict_g = [&](auto OWNZ, int cx, int cy, int p, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV],
-                         T (&dz)[NV]) {
+                         T (&rp)[ND][4], T (&dz)[NV]) {
         constexpr bool ownz = decltype(OWNZ)::value;
         const int s0 = (p + 2 * NR) % NR, sm = (p - 1 + 2 * NR) % NR, sp = (p + 1 + 2 * NR) % NR;
         const int hx = cx + H, hy = cy + H;
@@ -414,19 +414,19 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         const CellBG<T> bg = cell_bg<T, HSE>(bgT, p);
         if constexpr (ST == STAGE_HANCOCK) {
             if constexpr (NVS > NV)
-                hancock<T, ND, HSE, GZ, true>(w, dw, wh, hdt, inv_dx, gam, grav, bg, P(s0, NV, hy, hx));
+                hancock<T, ND, HSE, GZ, true>(w, dw, wh, rp, hdt, inv_dx, gam, grav, bg, P(s0, NV, hy, hx));
             else
-                hancock<T, ND, HSE, GZ>(w, dw, wh, hdt, inv_dx, gam, grav, bg);
+                hancock<T, ND, HSE, GZ>(w, dw, wh, rp, hdt, inv_dx, gam, grav, bg);
         } else {
-            mol_faces<T, ND, HSE>(w, dw, bg);
+            mol_faces<T, ND, HSE>(w, dw, bg, rp);
 #pragma unroll
             for (int q = 0; q < NV; ++q) wh[q] = w[q];
         }
     };
     constexpr bool OWNZ = sizeof(T) == 8 && RC == RECON_PLM;
     T dz[NV];
-    auto predict = [&](int cx, int cy, int p, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV]) {
-        predict_g(std::false_type{}, cx, cy, p, w, dw, wh, dz);
+    auto predict = [&](int cx, int cy, int p, T (&w)[NV], T (&dw)[ND][NV], T (&wh)[NV], T (&rp)[ND][4]) {
+        predict_g(std::false_type{}, cx, cy, p, w, dw, wh, rp, dz);
     };
 
     // ---- PPM face states of the cell at local (cx, cy) of plane p along
@@ -543,21 +543,21 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                 }
             }
         } else {
-            T w[NV], dw[ND][NV], wh[NV];
-            if constexpr (OWNZ) predict_g(std::true_type{}, tx, ty, p, w, dw, wh, dz);
-            else predict(tx, ty, p, w, dw, wh);
+            T w[NV], dw[ND][NV], wh[NV], rp[ND][4];
+            if constexpr (OWNZ) predict_g(std::true_type{}, tx, ty, p, w, dw, wh, rp, dz);
+            else predict(tx, ty, p, w, dw, wh, rp);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                zlo[q] = wh[q] - T(0.5) * dw[2][q];
-                ztop[q] = wh[q] + T(0.5) * dw[2][q];
+                zlo[q] = face_value<T, ND>(q, 2, false, wh, dw, rp);
+                ztop[q] = face_value<T, ND>(q, 2, true, wh, dw, rp);
             }
             if (xy) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    WX(wxl, q, ty, tx) = wh[q] - T(0.5) * dw[0][q];
-                    WX(wxh, q, ty, tx) = wh[q] + T(0.5) * dw[0][q];
-                    WY(wyl, q, ty, tx) = wh[q] - T(0.5) * dw[1][q];
-                    WY(wyh, q, ty, tx) = wh[q] + T(0.5) * dw[1][q];
+                    WX(wxl, q, ty, tx) = face_value<T, ND>(q, 0, false, wh, dw, rp);
+                    WX(wxh, q, ty, tx) = face_value<T, ND>(q, 0, true, wh, dw, rp);
+                    WY(wyl, q, ty, tx) = face_value<T, ND>(q, 1, false, wh, dw, rp);
+                    WY(wyh, q, ty, tx) = face_value<T, ND>(q, 1, true, wh, dw, rp);
                 }
             }
         }
@@ -585,23 +585,23 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                     }
                     continue;
                 }
-                T w[NV], dw[ND][NV], wh[NV];
-                predict(cx, cy, p, w, dw, wh);
+                T w[NV], dw[ND][NV], wh[NV], rp[ND][4];
+                predict(cx, cy, p, w, dw, wh, rp);
                 if (xside) {
                     if (cx < 0) {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) WX(wxh, q, cy, cx) = wh[q] + T(0.5) * dw[0][q];
+                        for (int q = 0; q < NV; ++q) WX(wxh, q, cy, cx) = face_value<T, ND>(q, 0, true, wh, dw, rp);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) WX(wxl, q, cy, cx) = wh[q] - T(0.5) * dw[0][q];
+                        for (int q = 0; q < NV; ++q) WX(wxl, q, cy, cx) = face_value<T, ND>(q, 0, false, wh, dw, rp);
                     }
                 } else {
                     if (cy < 0) {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) WY(wyh, q, cy, cx) = wh[q] + T(0.5) * dw[1][q];
+                        for (int q = 0; q < NV; ++q) WY(wyh, q, cy, cx) = face_value<T, ND>(q, 1, true, wh, dw, rp);
                     } else {
 #pragma unroll
-                        for (int q = 0; q < NV; ++q) WY(wyl, q, cy, cx) = wh[q] - T(0.5) * dw[1][q];
+                        for (int q = 0; q < NV; ++q) WY(wyl, q, cy, cx) = face_value<T, ND>(q, 1, false, wh, dw, rp);
                     }
                 }
             }
