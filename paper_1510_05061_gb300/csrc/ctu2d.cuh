@@ -165,30 +165,43 @@ __device__ __forceinline__ void ctu2d_body(const StepArgs &a, int tile, double d
             dw[1][q] = mc_slope(c - P(q, hy - 1, hx), P(q, hy + 1, hx) - c);
         }
         T wd[ND][NV];
+        // face densities and pressures {rho_lo, rho_hi, p_lo, p_hi} per axis,
+        // formed once for the positivity test and stored as faces
+        T rp[ND][4];
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
             predict_axis<T, ND>(w, dw[d], d, hdt, inv_dx[d], gam, grav, wd[d]);
-            ok = ok && positive(wd[d][0] - T(0.5) * dw[d][0]) && positive(wd[d][0] + T(0.5) * dw[d][0])
-                    && positive(wd[d][NV - 1] - T(0.5) * dw[d][NV - 1])
-                    && positive(wd[d][NV - 1] + T(0.5) * dw[d][NV - 1]);
+            rp[d][0] = wd[d][0] - T(0.5) * dw[d][0];
+            rp[d][1] = wd[d][0] + T(0.5) * dw[d][0];
+            rp[d][2] = wd[d][NV - 1] - T(0.5) * dw[d][NV - 1];
+            rp[d][3] = wd[d][NV - 1] + T(0.5) * dw[d][NV - 1];
+            ok = ok && positive(rp[d][0]) && positive(rp[d][1]) && positive(rp[d][2]) && positive(rp[d][3]);
         }
         if (!ok) {
             // zero slopes: every face takes the cell state plus half a step of gravity
 #pragma unroll
-            for (int d = 0; d < ND; ++d)
+            for (int d = 0; d < ND; ++d) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     dw[d][q] = T(0);
                     wd[d][q] = w[q] + (q >= 1 && q <= ND ? hdt * grav[q - 1] : T(0));
                 }
+                rp[d][0] = rp[d][1] = w[0];
+                rp[d][2] = rp[d][3] = w[NV - 1];
+            }
         }
+        auto face = [&](int d, int q, bool hi) -> T {
+            if (q == 0) return rp[d][hi ? 1 : 0];
+            if (q == NV - 1) return rp[d][hi ? 3 : 2];
+            return hi ? wd[d][q] + T(0.5) * dw[d][q] : wd[d][q] - T(0.5) * dw[d][q];
+        };
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            SE(sxl, q, cy, cx) = wd[0][q] - T(0.5) * dw[0][q];
-            SE(sxh, q, cy, cx) = wd[0][q] + T(0.5) * dw[0][q];
-            SE(syl, q, cy, cx) = wd[1][q] - T(0.5) * dw[1][q];
-            SE(syh, q, cy, cx) = wd[1][q] + T(0.5) * dw[1][q];
+            SE(sxl, q, cy, cx) = face(0, q, false);
+            SE(sxh, q, cy, cx) = face(0, q, true);
+            SE(syl, q, cy, cx) = face(1, q, false);
+            SE(syh, q, cy, cx) = face(1, q, true);
         }
     }
     __syncthreads();

@@ -220,24 +220,27 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
                 dw[2][q] = mc_slope(c - P(sm, q, hy, hx), P(sp, q, hy, hx) - c);
             }
             T wd[ND][NV];
+            // face densities and pressures {rho_lo, rho_hi, p_lo, p_hi} per
+            // axis, formed once for the positivity test and stored as faces
+            T rp[ND][4];
             bool ok = true;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
+                if constexpr (HSE) predict_axis_bg<T>(w, dw[d], d, hdt, inv_dx[d], gam, grav, bg, wd[d]);
+                else predict_axis<T, ND>(w, dw[d], d, hdt, inv_dx[d], gam, grav, wd[d]);
+                rp[d][0] = wd[d][0] - T(0.5) * dw[d][0];
+                rp[d][1] = wd[d][0] + T(0.5) * dw[d][0];
+                rp[d][2] = wd[d][NV - 1] - T(0.5) * dw[d][NV - 1];
+                rp[d][3] = wd[d][NV - 1] + T(0.5) * dw[d][NV - 1];
                 if constexpr (HSE) {
-                    predict_axis_bg<T>(w, dw[d], d, hdt, inv_dx[d], gam, grav, bg, wd[d]);
                     // total face density and pressure: the plane's centre
                     // background for x and y, the z faces' own along z
                     const T rlo = d == 2 ? bg.rho_lo : bg.rho, rhi = d == 2 ? bg.rho_hi : bg.rho;
                     const T plo = d == 2 ? bg.p_lo : bg.p, phi = d == 2 ? bg.p_hi : bg.p;
-                    ok = ok && positive(rlo + (wd[d][0] - T(0.5) * dw[d][0]))
-                            && positive(rhi + (wd[d][0] + T(0.5) * dw[d][0]))
-                            && positive(plo + (wd[d][NV - 1] - T(0.5) * dw[d][NV - 1]))
-                            && positive(phi + (wd[d][NV - 1] + T(0.5) * dw[d][NV - 1]));
+                    ok = ok && positive(rlo + rp[d][0]) && positive(rhi + rp[d][1])
+                            && positive(plo + rp[d][2]) && positive(phi + rp[d][3]);
                 } else {
-                    predict_axis<T, ND>(w, dw[d], d, hdt, inv_dx[d], gam, grav, wd[d]);
-                    ok = ok && positive(wd[d][0] - T(0.5) * dw[d][0]) && positive(wd[d][0] + T(0.5) * dw[d][0])
-                            && positive(wd[d][NV - 1] - T(0.5) * dw[d][NV - 1])
-                            && positive(wd[d][NV - 1] + T(0.5) * dw[d][NV - 1]);
+                    ok = ok && positive(rp[d][0]) && positive(rp[d][1]) && positive(rp[d][2]) && positive(rp[d][3]);
                 }
             }
             if (!ok) {
@@ -261,13 +264,20 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
                         const T gq = q >= 1 && q <= ND ? (d == 2 ? gz[q - 1] : grav[q - 1]) : T(0);
                         wd[d][q] = w[q] + (q >= 1 && q <= ND ? hdt * gq : T(0));
                     }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    rp[d][0] = rp[d][1] = w[0];
+                    rp[d][2] = rp[d][3] = w[NV - 1];
+                }
             }
 #pragma unroll
             for (int d = 0; d < ND; ++d)
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    SE(b, 2 * d, q, cy, cx) = wd[d][q] - T(0.5) * dw[d][q];
-                    SE(b, 2 * d + 1, q, cy, cx) = wd[d][q] + T(0.5) * dw[d][q];
+                    const bool rq = q == 0 || q == NV - 1;
+                    const int k = q == 0 ? 0 : 2;
+                    SE(b, 2 * d, q, cy, cx) = rq ? rp[d][k] : wd[d][q] - T(0.5) * dw[d][q];
+                    SE(b, 2 * d + 1, q, cy, cx) = rq ? rp[d][k + 1] : wd[d][q] + T(0.5) * dw[d][q];
                 }
         }
     };
