@@ -331,11 +331,10 @@ __device__ __forceinline__ void ctu2d_body(const StepArgs &a, int tile, double d
 #pragma unroll
         for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
         const T rinv = rcp_t(u[0]);
-        const T vx = u[1] * rinv, vy = u[2] * rinv;
         const T pres = (gam - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
         const T gp = gam * pres;
         const T cs = gp * rsqrt_t(gp * u[0]);
-        const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1];
+        const T s = signal_speed<T, 2>(u + 1, rinv, cs, inv_dx);
         if (!(u[0] > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
         else smax = s;
     }

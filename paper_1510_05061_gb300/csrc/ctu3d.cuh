@@ -509,12 +509,11 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
             const T rho = HSE ? bgT[p + 1].rho_c + u[0] : u[0];
             const T rinv = rcp_t(rho);
-            const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
             const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
             const T pres = HSE ? bgT[p + 1].p_c + pp : pp;
             const T gp = gam * pres;
             const T cs = gp * rsqrt_t(gp * rho);
-            const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
+            const T s = signal_speed<T, 3>(u + 1, rinv, cs, inv_dx);
             if (!positive(rho) || !positive(pres) || !isfinite(s)) bad = true;
             else smax = max_t(smax, s);
         }

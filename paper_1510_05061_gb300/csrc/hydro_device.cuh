@@ -118,15 +118,15 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 // p = (gamma - 1)(E - |m|^2 / (2 rho)) from the momentum components m, the
-// total energy e, rinv = 1/rho and gm1 = gamma - 1: |m|^2 summed in axis
-// order, then (gamma - 1) fma(-1/2, |m|^2 / rho, E).
+// velocities u = m / rho, the total energy e and gm1 = gamma - 1: |m|^2 / rho
+// as u . m summed in axis order, then (gamma - 1) fma(-1/2, u . m, E).
 template <typename T, int ND>
-__device__ __forceinline__ T pressure_of(const T (&m)[ND], T e, T rinv, T gm1)
+__device__ __forceinline__ T pressure_of(const T (&m)[ND], const T (&u)[ND], T e, T gm1)
 {
-    T k = mul_rn(m[0], m[0]);
+    T k = mul_rn(u[0], m[0]);
 #pragma unroll
-    for (int d = 1; d < ND; ++d) k = fma_rn(m[d], m[d], k);
-    return mul_rn(gm1, fma_rn(T(-0.5), mul_rn(k, rinv), e));
+    for (int d = 1; d < ND; ++d) k = fma_rn(u[d], m[d], k);
+    return mul_rn(gm1, fma_rn(T(-0.5), k, e));
 }
 
 // A step constant in the kernel's precision: the FP64 value, or its FP32
@@ -212,6 +212,23 @@ __device__ __forceinline__ double mc_slope(double dl, double dr)
     return same ? copysign(a, dr) : 0.0;
 }
 
+// CFL signal speed of a cell, sum_d (|u_d| + c) / dx_d, from its momenta m
+// (ND components), rinv = 1/rho and sound speed c, arranged as
+// (sum_d |m_d| / dx_d) / rho + c sum_d 1/dx_d (the sum of the 1/dx_d is
+// loop-invariant in the callers).
+template <typename T, int ND>
+__device__ __forceinline__ T signal_speed(const T *m, T rinv, T c, const T (&inv_dx)[3])
+{
+    T a = fabs(m[0]) * inv_dx[0];
+    T sidx = inv_dx[0];
+#pragma unroll
+    for (int d = 1; d < ND; ++d) {
+        a = fma(fabs(m[d]), inv_dx[d], a);
+        sidx += inv_dx[d];
+    }
+    return fma(rinv, a, c * sidx);
+}
+
 // Background seen by one cell in HSE mode (all zero in plain mode).
 template <typename T>
 struct CellBG {
@@ -289,25 +306,28 @@ __device__ __forceinline__ bool hancock(const T (&w)[ND + 2], T (&dw)[ND][ND + 2
     // RINV: 1/rho as computed when the cell was staged (the same value)
     const T rinv = RINV ? rinv_given : rcp_t(rho);
     const T gp = gam * pr;
-    T rate[NV];
+    // A_d(w) dw_d / dx_d summed over d: rho: u_d drho_d + rho du_{d,d};
+    // u_e: u_d du_{e,d} (+ dp_d / rho for e = d); p: u_d dp_d + gamma p du_{d,d}.
+    // The rho and p rows take their normal-velocity terms through one
+    // divergence, div u = sum_d du_{d,d} / dx_d; 1/dx_d is folded into the
+    // other coefficients.
+    T divu = dw[0][1] * inv_dx[0];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) rate[q] = T(0);
-    // A_d(w) dw_d / dx_d summed over d, with 1/dx_d folded into the
-    // coefficients: rho: u_n drho + rho du_n; u_e: u_n du_e (+ dp/rho for
-    // e = d); p: u_n dp + gamma p du_n
+    for (int d = 1; d < ND; ++d) divu = fma(dw[d][1 + d], inv_dx[d], divu);
+    T rate[NV];
+    rate[0] = -rho * divu;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) rate[1 + e] = T(0);
+    rate[NV - 1] = -gp * divu;
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         const T un_dx = w[1 + d] * inv_dx[d];
-        const T rho_dx = rho * inv_dx[d];
         const T rinv_dx = rinv * inv_dx[d];
-        const T gp_dx = gp * inv_dx[d];
         rate[0] = fma(-un_dx, dw[d][0], rate[0]);
-        rate[0] = fma(-rho_dx, dw[d][1 + d], rate[0]);
 #pragma unroll
         for (int e = 0; e < ND; ++e) rate[1 + e] = fma(-un_dx, dw[d][1 + e], rate[1 + e]);
         rate[1 + d] = fma(-rinv_dx, dw[d][NV - 1], rate[1 + d]);
         rate[NV - 1] = fma(-un_dx, dw[d][NV - 1], rate[NV - 1]);
-        rate[NV - 1] = fma(-gp_dx, dw[d][1 + d], rate[NV - 1]);
     }
     // gravity on the velocities: g rho'/rho - B/rho in HSE mode, g otherwise
     T gsrc[ND];

@@ -147,11 +147,12 @@ __device__ __forceinline__ void pair3d_body(const StepArgs &a, int tile, int chu
         const float rho = HSE ? rho_bg + r : r;
         const float rinv = rcp_t(rho);
         const float m[3] = {m0, m1, m2};
+        const float u[3] = {mul_rn(m0, rinv), mul_rn(m1, rinv), mul_rn(m2, rinv)};
         o[0] = r;
-        o[1] = mul_rn(m0, rinv);
-        o[2] = mul_rn(m1, rinv);
-        o[3] = mul_rn(m2, rinv);
-        o[4] = pressure_of<float, 3>(m, v[4], rinv, gam - 1.0f);
+        o[1] = u[0];
+        o[2] = u[1];
+        o[3] = u[2];
+        o[4] = pressure_of<float, 3>(m, u, v[4], gam - 1.0f);
     };
     auto stage = [&](int pz) {
         bool fz;

@@ -82,10 +82,11 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
     auto convert = [&](T r, T m0, T m1, T e, int hy, int hx) {
         const T rinv = rcp_t(r);
         const T m[2] = {m0, m1};
+        const T u[2] = {mul_rn(m0, rinv), mul_rn(m1, rinv)};
         P(0, hy, hx) = r;
-        P(1, hy, hx) = mul_rn(m0, rinv);
-        P(2, hy, hx) = mul_rn(m1, rinv);
-        P(3, hy, hx) = pressure_of<T, 2>(m, e, rinv, gam - T(1));
+        P(1, hy, hx) = u[0];
+        P(2, hy, hx) = u[1];
+        P(3, hy, hx) = pressure_of<T, 2>(m, u, e, gam - T(1));
     };
     constexpr int W = 16 / sizeof(T);
     constexpr int NQ = TX / W + 2;
@@ -303,11 +304,10 @@ __device__ __forceinline__ void step2d_body(const StepArgs &a, int tile, double 
 #pragma unroll
         for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
         const T rinv = rcp_t(u[0]);
-        const T vx = u[1] * rinv, vy = u[2] * rinv;
         const T pres = (gam - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
         const T gp = gam * pres;
         const T cs = gp * rsqrt_t(gp * u[0]);
-        const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1];
+        const T s = signal_speed<T, 2>(u + 1, rinv, cs, inv_dx);
         if (!(u[0] > T(0)) || !(pres > T(0)) || !isfinite(s)) bad = true;
         else smax = s;
     }

@@ -257,11 +257,12 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         const T rho = HSE ? rho_bg + r : r;
         const T rinv = rcp_t(rho);
         const T m[3] = {m0, m1, m2};
+        const T u[3] = {mul_rn(m0, rinv), mul_rn(m1, rinv), mul_rn(m2, rinv)};
         o[0] = r;
-        o[1] = mul_rn(m0, rinv);
-        o[2] = mul_rn(m1, rinv);
-        o[3] = mul_rn(m2, rinv);
-        o[4] = pressure_of<T, 3>(m, v[4], rinv, gam - T(1));
+        o[1] = u[0];
+        o[2] = u[1];
+        o[3] = u[2];
+        o[4] = pressure_of<T, 3>(m, u, v[4], gam - T(1));
         if constexpr (NVS > NV) o[NV] = rinv;
     };
     // the W cells of vector k of row hy, converted, as pairs (the two FP32
@@ -800,12 +801,11 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             // CFL signal speed and admissibility of the new state
             const T rho = HSE ? bgR + u[0] : u[0];
             const T rinv = rcp_t(rho);
-            const T vx = u[1] * rinv, vy = u[2] * rinv, vz = u[3] * rinv;
             const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
             const T pres = HSE ? bgP + pp : pp;
             const T gp = gam * pres;
             const T cs = gp * rsqrt_t(gp * rho);
-            const T s = (fabs(vx) + cs) * inv_dx[0] + (fabs(vy) + cs) * inv_dx[1] + (fabs(vz) + cs) * inv_dx[2];
+            const T s = signal_speed<T, 3>(u + 1, rinv, cs, inv_dx);
             if (!positive(rho) || !positive(pres) || !isfinite(s)) bad = true;
             else smax = max_t(smax, s);
         }
