@@ -429,10 +429,17 @@ __device__ __forceinline__ void ppm_faces(T am, T a, T ap, T sm, T s, T sp, T &l
 // S_R <= 0 -> F_R.  igm1 = 1/(gamma - 1).
 //
 // Arithmetic is arranged to need two square-root reciprocals and two
-// divisions per face: c = g rsqrt(g rho) with g = gamma p, and with
-// q = 1/(S_K - S*) the star state U*_K = q (rho_K (S_K - u_K)) [1, S*, v_t]
-// and E*_K = q [(S_K - u_K) E_K + (S* - u_K)(rho_K (S_K - u_K) S* + p_K)],
-// which is the star state of Toro eq. (10.39) multiplied out.
+// divisions per face: c = g rsqrt(g rho) with g = gamma p.  The star state of
+// Toro eq. (10.39), rho*_K = rho_K (S_K - u_K) / (S_K - S*) with velocity
+// (S*, v_t) and E*_K = rho*_K [E_K / rho_K + (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))],
+// enters only through F*_K = F_K + S_K (U*_K - U_K), whose components reduce
+// to multiples of one factor h = S_K (S* - u_K) / (S_K - S*):
+//   S_K (rho*_K - rho_K)             = rho_K h                      (= c0)
+//   S_K (rho*_K v_t - rho_K v_t)     = c0 v_t
+//   S_K (rho*_K S* - rho_K u_K)      = S_K c0
+//   S_K (E*_K - E_K)                 = h (E_K + p_K + m_K S*),  m_K = rho_K (S_K - u_K)
+// (rho*_K - rho_K = rho_K (S* - u_K) / (S_K - S*); the energy line follows
+// from E*_K - E_K written over the common denominator S_K - S*).
 template <typename T, int ND, int D, bool HSE>
 __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2], T rb, T pb,
                                      T gam, T igm1, T (&f)[ND + 2])
@@ -465,6 +472,7 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     const T pk = left ? pl : pr;
     const T ppk = left ? wl[NV - 1] : wr[NV - 1];
     const T sk = left ? sl : sr;
+    const T mk = left ? ml : mr;
     T vk[ND];
 #pragma unroll
     for (int e = 0; e < ND; ++e) vk[e] = left ? wl[1 + e] : wr[1 + e];
@@ -472,7 +480,8 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     T ke = T(0);
 #pragma unroll
     for (int e = 0; e < ND; ++e) ke += vk[e] * vk[e];
-    const T Ek = pk * igm1 + T(0.5) * rk * ke;
+    // E_K + p_K = p_K gamma / (gamma - 1) + rho_K |v_K|^2 / 2
+    const T hk = fma(pk, igm1 + T(1), T(0.5) * rk * ke);
 
     // Euler flux of the chosen side
     const T mflux = rk * uk;
@@ -480,37 +489,28 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
 #pragma unroll
     for (int e = 0; e < ND; ++e) f[1 + e] = mflux * vk[e];
     f[1 + D] += ppk;
-    f[NV - 1] = uk * (Ek + pk);
+    f[NV - 1] = uk * hk;
 
     // F*_K = F_K + S_K (U*_K - U_K), applied only inside the fan
-    const T skmu = sk - uk;
-    const T q = rcp_t(sk - sstar);
-    const T mk = rk * skmu;
-    const T fac = mk * q;
-    const T e_star = q * (skmu * Ek + (sstar - uk) * (mk * sstar + pk));
-    const T c0 = sk * (fac - rk);           // S_K (rho*_K - rho_K)
+    const T h = (sk * rcp_t(sk - sstar)) * (sstar - uk);
+    const T c0 = rk * h;                    // S_K (rho*_K - rho_K)
+    const T fE = fma(h, fma(mk, sstar, hk), f[NV - 1]);
     if constexpr (sizeof(T) == 8) {
         // FP64 (bound by its FP64 pipe): each star component formed by one
-        // fused multiply-add onto F_K and selected, four FP64 instructions
-        // fewer per face than adding a selected correction
+        // fused multiply-add onto F_K (or one addition) and selected
         f[0] = star ? f[0] + c0 : f[0];
 #pragma unroll
         for (int e = 0; e < ND; ++e) {
-            const T fs = (e == D) ? fma(sk, fma(fac, sstar, -mflux), f[1 + e]) : fma(c0, vk[e], f[1 + e]);
+            const T fs = (e == D) ? fma(sk, c0, f[1 + e]) : fma(c0, vk[e], f[1 + e]);
             f[1 + e] = star ? fs : f[1 + e];
         }
-        const T fE = fma(sk, e_star - Ek, f[NV - 1]);
         f[NV - 1] = star ? fE : f[NV - 1];
     } else {
-        f[0] += star ? c0 : T(0);
+        const T cs = star ? c0 : T(0);
+        f[0] += cs;
 #pragma unroll
-        for (int e = 0; e < ND; ++e) {
-            // transverse: S_K (rho*_K - rho_K) v_e; normal: S_K (rho*_K S* - rho_K u_K)
-            const T ce = (e == D) ? sk * (fac * sstar - mflux) : c0 * vk[e];
-            f[1 + e] += star ? ce : T(0);
-        }
-        const T cE = sk * (e_star - Ek);
-        f[NV - 1] += star ? cE : T(0);
+        for (int e = 0; e < ND; ++e) f[1 + e] = fma(cs, (e == D) ? sk : vk[e], f[1 + e]);
+        f[NV - 1] = star ? fE : f[NV - 1];
     }
 }
 
