@@ -149,8 +149,9 @@ __device__ __forceinline__ void hancock2(const f2 (&w)[5], f2 (&dw)[3][5], f2 (&
 // HLLC flux along axis D (Toro, 3rd ed., sec. 10.4-10.6) of a pair of
 // faces, Davis wave speeds, branch tie S* = 0 to the left; (rb, pb) the
 // background at the faces (zero in plain mode), the normal momentum flux
-// carries p'.  The star state is multiplied out as in hllc() of
-// hydro_device.cuh, and the fan's branch is applied by per-lane selects.
+// carries p'.  The star correction is formed through the factor
+// h = S_K (S* - u_K) / (S_K - S*) as in hllc() of hydro_device.cuh, and the
+// fan's branch is applied by per-lane selects.
 template <int D, bool HSE>
 __device__ __forceinline__ void hllc2(const f2 (&wl)[5], const f2 (&wr)[5], float rb, float pb, float gam,
                                       float igm1, f2 (&f)[5])
@@ -181,12 +182,14 @@ __device__ __forceinline__ void hllc2(const f2 (&wl)[5], const f2 (&wr)[5], floa
     const f2 pk = sel2(left, pl, prr);
     const f2 ppk = sel2(left, wl[4], wr[4]);
     const f2 sk = sel2(left, sl, sr);
+    const f2 mk = sel2(left, ml, mr);
     f2 vk[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) vk[e] = sel2(left, wl[1 + e], wr[1 + e]);
     const f2 uk = vk[D];
     const f2 ke = fma2(vk[2], vk[2], fma2(vk[1], vk[1], mul2(vk[0], vk[0])));
-    const f2 Ek = fma2(pk, bc(igm1), mul2(mul2(bc(0.5f), rk), ke));
+    // E_K + p_K = p_K gamma / (gamma - 1) + rho_K |v_K|^2 / 2
+    const f2 hk = fma2(pk, bc(igm1 + 1.0f), mul2(mul2(bc(0.5f), rk), ke));
 
     // Euler flux of the chosen side
     const f2 mflux = mul2(rk, uk);
@@ -194,22 +197,18 @@ __device__ __forceinline__ void hllc2(const f2 (&wl)[5], const f2 (&wr)[5], floa
 #pragma unroll
     for (int e = 0; e < 3; ++e) f[1 + e] = mul2(mflux, vk[e]);
     f[1 + D] = add2(f[1 + D], ppk);
-    f[4] = mul2(uk, add2(Ek, pk));
+    f[4] = mul2(uk, hk);
 
     // F*_K = F_K + S_K (U*_K - U_K), applied only inside the fan
-    const f2 skmu = sub2(sk, uk);
-    const f2 q = rcp2(sub2(sk, sstar));
-    const f2 mk = mul2(rk, skmu);
-    const f2 fac = mul2(mk, q);
-    const f2 e_star = mul2(q, fma2(skmu, Ek, mul2(sub2(sstar, uk), fma2(mk, sstar, pk))));
-    const f2 c0 = mul2(sk, sub2(fac, rk));             // S_K (rho*_K - rho_K)
+    const f2 h = mul2(mul2(sk, rcp2(sub2(sk, sstar))), sub2(sstar, uk));
+    const f2 c0 = mul2(rk, h);                         // S_K (rho*_K - rho_K)
     f[0] = sel2(star, add2(f[0], c0), f[0]);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        const f2 fs = (e == D) ? fma2(sk, sub2(mul2(fac, sstar), mflux), f[1 + e]) : fma2(c0, vk[e], f[1 + e]);
+        const f2 fs = fma2(c0, (e == D) ? sk : vk[e], f[1 + e]);
         f[1 + e] = sel2(star, fs, f[1 + e]);
     }
-    f[4] = sel2(star, fma2(sk, sub2(e_star, Ek), f[4]), f[4]);
+    f[4] = sel2(star, fma2(h, fma2(mk, sstar, hk), f[4]), f[4]);
 }
 
 }  // namespace hydro

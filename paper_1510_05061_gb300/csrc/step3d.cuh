@@ -94,7 +94,16 @@ struct Step3DSmem {
     // reciprocal of its own)
     static constexpr int NVS = (sizeof(T) == 8 && RC == RECON_PLM) ? NV + 1 : NV;
     static constexpr size_t plane = (size_t)NVS * HY * HXS;
-    static constexpr size_t rest = 2 * wx + 2 * wy + fx + fy + raw;
+    // FP64 PLM: the x and y differences of adjacent staged primitives, each
+    // formed once per plane and read by both cells beside it (two planes:
+    // the one the half step reads and the next, formed in the same barrier
+    // interval).  x: rows -1..TY, faces -2..TX (the face between cells f and
+    // f + 1); y: faces -2..TY, columns -1..TX.
+    static constexpr bool diffs = sizeof(T) == 8 && RC == RECON_PLM;
+    static constexpr size_t dxn = (size_t)NV * (TY + 2) * (TX + 3);
+    static constexpr size_t dyn = (size_t)NV * (TY + 3) * (TX + 2);
+    static constexpr size_t dif = diffs ? 2 * (dxn + dyn) : 0;
+    static constexpr size_t rest = 2 * wx + 2 * wy + fx + fy + dif + raw;
     // (fits: one CTA's limit, and the tile's resident CTAs per SM, each with
     // about 1.5 KB of reserved and static shared memory, in the SM's 228 KB).
     // Measured on GB300: +4..+21 % for the synchronous FP32 tiles and +4 %
@@ -165,8 +174,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     T *wxl = prim + S::prim, *wxh = wxl + S::wx;
     T *wyl = wxh + S::wx, *wyh = wyl + S::wy;
     T *fxs = wyh + S::wy, *fys = fxs + S::fx;
+    T *dif = fys + S::fy;
     // (16-byte aligned: the vector copies land there)
-    T *rawbuf = reinterpret_cast<T *>((reinterpret_cast<unsigned long long>(fys + S::fy) + 15ull) & ~15ull);
+    T *rawbuf = reinterpret_cast<T *>((reinterpret_cast<unsigned long long>(dif + S::dif) + 15ull) & ~15ull);
 
     const int nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
@@ -388,6 +398,39 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         }
     };
 
+    // ---- x and y differences of plane pz (FP64 PLM; S::diffs): entry f of
+    // a row is P(f + 1) - P(f), the same operands and operation as the
+    // slope's own differences, so the slopes keep their bits.  Formed once
+    // per face instead of once for each of the two cells beside it.
+    constexpr bool DIFFS = S::diffs;
+    constexpr int DXR = TX + 3, DYR = TX + 2;
+    constexpr int NDX = (TY + 2) * DXR, NDY = (TY + 3) * DYR;
+    auto DX = [&](int pz, int q, int cy, int f) -> T & {   // cy in [-1, TY], f in [-2, TX]
+        return dif[(pz & 1) * (S::dxn + S::dyn) + (q * (TY + 2) + cy + 1) * DXR + f + 2];
+    };
+    auto DY = [&](int pz, int q, int f, int cx) -> T & {   // f in [-2, TY], cx in [-1, TX]
+        return dif[(pz & 1) * (S::dxn + S::dyn) + S::dxn + (q * (TY + 3) + f + 2) * DYR + cx + 1];
+    };
+    auto form_diffs = [&](int pz) {
+        const int sl = (pz + 2 * NR) % NR;
+        // (the items past the second pass land on warps 2, 3, ...: warps 0
+        // and 1 hold the ring cells' half steps)
+        for (int i = rotated_start<NT>(tid); i < NDX + NDY; i += NT) {
+            if (i < NDX) {
+                const int cy = i / DXR - 1, f = i % DXR - 2;
+#pragma unroll
+                for (int q = 0; q < NV; ++q)
+                    DX(pz, q, cy, f) = P(sl, q, cy + H, f + 1 + H) - P(sl, q, cy + H, f + H);
+            } else {
+                const int j = i - NDX;
+                const int f = j / DYR - 2, cx = j % DYR - 1;
+#pragma unroll
+                for (int q = 0; q < NV; ++q)
+                    DY(pz, q, f, cx) = P(sl, q, f + 1 + H, cx + H) - P(sl, q, f + H, cx + H);
+            }
+        }
+    };
+
     // ---- slopes + half step of the cell at local (cx, cy) of plane p.
     // OWNZ (FP64, the thread's own column): the z difference below plane p
     // is the one above plane p-1, kept in dz from the previous plane (the
@@ -402,8 +445,13 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
         for (int q = 0; q < NV; ++q) {
             const T c = P(s0, q, hy, hx);
             w[q] = c;
-            dw[0][q] = mc_slope(c - P(s0, q, hy, hx - 1), P(s0, q, hy, hx + 1) - c);
-            dw[1][q] = mc_slope(c - P(s0, q, hy - 1, hx), P(s0, q, hy + 1, hx) - c);
+            if constexpr (DIFFS) {
+                dw[0][q] = mc_slope(DX(p, q, cy, cx - 1), DX(p, q, cy, cx));
+                dw[1][q] = mc_slope(DY(p, q, cy - 1, cx), DY(p, q, cy, cx));
+            } else {
+                dw[0][q] = mc_slope(c - P(s0, q, hy, hx - 1), P(s0, q, hy, hx + 1) - c);
+                dw[1][q] = mc_slope(c - P(s0, q, hy - 1, hx), P(s0, q, hy + 1, hx) - c);
+            }
             if constexpr (ownz) {
                 const T dr = P(sp, q, hy, hx) - c;
                 dw[2][q] = mc_slope(dz[q], dr);
@@ -480,6 +528,10 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     }
     __syncthreads();
     if constexpr (ASYNC) fetch(z0 + LEAD - 1);
+    if constexpr (DIFFS) {
+        form_diffs(z0 - 1);
+        __syncthreads();
+    }
     if constexpr (OWNZ) {
         // the own column's z difference below plane z0-1 (planes staged above)
 #pragma unroll
@@ -607,6 +659,10 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
                 }
             }
         }
+        // the next plane's differences (staged and visible since the last
+        // barrier) for the next iteration's half step
+        if constexpr (DIFFS)
+            if (p + 1 <= z1) form_diffs(p + 1);
         __syncthreads();
 
         // ---- step 3: face fluxes.  Each thread evaluates the low x face and
