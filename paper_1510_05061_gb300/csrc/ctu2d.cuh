@@ -331,7 +331,7 @@ __device__ __forceinline__ void ctu2d_body(const StepArgs &a, int tile, double d
 #pragma unroll
         for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
         const T rinv = rcp_t(u[0]);
-        const T pres = (gam - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
+        const T pres = (gam - T(1)) * (u[3] - half_nonneg(u[1] * u[1] + u[2] * u[2]) * rinv);
         const T gp = gam * pres;
         const T cs = gp * rsqrt_t(gp * u[0]);
         const T s = signal_speed<T, 2>(u + 1, rinv, cs, inv_dx);

@@ -497,10 +497,10 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             const T r_old = u[0];
             const T r_new = r_old + dt * du[0];
             u[0] = r_new;
-            const T rsum = T(0.5) * (r_old + r_new);
+            const T rsum = r_old + r_new;   // (the half is folded into g / 2)
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                T src = grav[d] * rsum;
+                T src = (T(0.5) * grav[d]) * rsum;
                 if (HSE && d == 2) src -= bgT[p + 1].B;
                 u[1 + d] += dt * (du[1 + d] + src);
             }
@@ -509,7 +509,7 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
             for (int q = 0; q < NV; ++q) Un[c + q * vs] = u[q];
             const T rho = HSE ? bgT[p + 1].rho_c + u[0] : u[0];
             const T rinv = rcp_t(rho);
-            const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
+            const T pp = (gam - T(1)) * (u[4] - half_nonneg(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
             const T pres = HSE ? bgT[p + 1].p_c + pp : pp;
             const T gp = gam * pres;
             const T cs = gp * rsqrt_t(gp * rho);

@@ -154,6 +154,17 @@ __device__ __forceinline__ int rotated_start(int tid)
 // an integer test of the bit pattern, which keeps it off the FP64 pipe.
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return x > 0.0f; }
+// x / 2 of a non-negative x.  For doubles an exact halving on the integer
+// pipe (one off the exponent field; the same bits as 0.5 * x for normal
+// results) rather than on the FP64 pipe: 0 for x below 2^-1021, where the
+// half would not be normal; infinities and NaNs are passed through.
+__device__ __forceinline__ double half_nonneg(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const long long h = b >= (2ll << 52) ? b - (1ll << 52) : 0ll;
+    return __longlong_as_double(b >= (0x7ffll << 52) ? b : h);
+}
+__device__ __forceinline__ float half_nonneg(float x) { return 0.5f * x; }
 // Sign tests for the HLLC fan branches: x >= 0 and x <= 0 as numeric
 // comparisons (both zeros satisfy both), done on the bit pattern for doubles:
 // x >= 0 holds for a clear sign bit and for -0 (whose pattern is the most
@@ -453,8 +464,12 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     const T gpl = gam * pl, gpr = gam * pr;
     const T cl = gpl * rsqrt_t(gpl * rl);
     const T cr = gpr * rsqrt_t(gpr * rr);
-    const T sl = min_t(ul - cl, ur - cr);
-    const T sr = max_t(ul + cl, ur + cr);
+    // S_L - u_L = min(-c_L, (u_R - u_L) - c_R) and S_R - u_R = max(c_L - (u_R - u_L), c_R):
+    // the offsets the star factors m_K = rho_K (S_K - u_K) need, and S_L, S_R from them
+    const T du = ur - ul;
+    const T al = min_t(-cl, du - cr);
+    const T ar = max_t(cl - du, cr);
+    const T sl = ul + al, sr = ur + ar;
 
     // Branch-free: every face computes S* and the star correction and the
     // branch of the HLLC fan is applied by selects.  The chosen branch's
@@ -462,7 +477,7 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
     // a thread's independent faces interleave.  S* and 1/(S_K - S*) are
     // finite for positive densities and pressures (S_L < u_L, S_R > u_R).
     const T dpp = wr[NV - 1] - wl[NV - 1];   // background cancels in the difference
-    const T ml = rl * (sl - ul), mr = rr * (sr - ur);
+    const T ml = rl * al, mr = rr * ar;
     const T sstar = div_t(dpp + ml * ul - mr * ur, ml - mr);
     const bool sup_l = nonnegative(sl);     // whole fan moves right: F_L
     const bool sup_r = nonpositive(sr);     // whole fan moves left: F_R
@@ -481,7 +496,7 @@ __device__ __forceinline__ void hllc(const T (&wl)[ND + 2], const T (&wr)[ND + 2
 #pragma unroll
     for (int e = 0; e < ND; ++e) ke += vk[e] * vk[e];
     // E_K + p_K = p_K gamma / (gamma - 1) + rho_K |v_K|^2 / 2
-    const T hk = fma(pk, igm1 + T(1), T(0.5) * rk * ke);
+    const T hk = fma(pk, igm1 + T(1), rk * half_nonneg(ke));
 
     // Euler flux of the chosen side
     const T mflux = rk * uk;

@@ -836,13 +836,14 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             u[0] = r_new;
             // gravity on the momentum: time-centred density (MUSCL-Hancock)
             // or the stage's density (Runge-Kutta stages)
-            const T rsum = ST == STAGE_HANCOCK ? T(0.5) * (r_old + r_new) : r_old;
+            // (the half of the time-centred density is folded into g / 2)
+            const T rsum = ST == STAGE_HANCOCK ? r_old + r_new : r_old;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 if (GZ && d < 2) {
                     u[1 + d] += dt * du[1 + d];
                 } else {
-                    T src = grav[d] * rsum;
+                    T src = (ST == STAGE_HANCOCK ? T(0.5) * grav[d] : grav[d]) * rsum;
                     if (HSE && d == 2) src -= bgB;
                     u[1 + d] += dt * (du[1 + d] + src);
                 }
@@ -857,7 +858,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             // CFL signal speed and admissibility of the new state
             const T rho = HSE ? bgR + u[0] : u[0];
             const T rinv = rcp_t(rho);
-            const T pp = (gam - T(1)) * (u[4] - T(0.5) * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
+            const T pp = (gam - T(1)) * (u[4] - half_nonneg(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * rinv);
             const T pres = HSE ? bgP + pp : pp;
             const T gp = gam * pres;
             const T cs = gp * rsqrt_t(gp * rho);
