@@ -686,52 +686,7 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             }
         };
         T fz[NV];
-        if constexpr (sizeof(T) == 8) {
-            // FP64 is register-bound (one CTA per SM): one face at a time
-            if (xy) {
-                for (int i = tid; i < (TX + 1) * TY; i += NT) {
-                    const int fi = i % (TX + 1), cy = i / (TX + 1);
-                    T wl[NV], wr[NV], f[NV];
-                    const int gf = x0 + fi;
-                    const bool w_lo = gf == 0 && a.bc_lo[0] == BC_REFLECT;
-                    const bool w_hi = gf == nx && a.bc_hi[0] == BC_REFLECT;
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        const T xl = WX(wxh, q, cy, fi - 1), xr = WX(wxl, q, cy, fi);
-                        wl[q] = w_lo ? (q == 1 ? -xr : xr) : xl;
-                        wr[q] = w_hi ? (q == 1 ? -xl : xl) : xr;
-                    }
-                    hllc<T, ND, 0, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) FX(q, cy, fi) = f[q];
-                }
-                // (the second pass on warp 2: warp 0 holds the x faces')
-                for (int i = rotated_start<NT>(tid); i < TX * (TY + 1); i += NT) {
-                    const int cx = i % TX, fi = i / TX;
-                    T wl[NV], wr[NV], f[NV];
-                    const int gf = y0 + fi;
-                    const bool w_lo = gf == 0 && a.bc_lo[1] == BC_REFLECT;
-                    const bool w_hi = gf == ny && a.bc_hi[1] == BC_REFLECT;
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        const T yl = WY(wyh, q, fi - 1, cx), yr = WY(wyl, q, fi, cx);
-                        wl[q] = w_lo ? (q == 2 ? -yr : yr) : yl;
-                        wr[q] = w_hi ? (q == 2 ? -yl : yl) : yr;
-                    }
-                    hllc<T, ND, 1, HSE>(wl, wr, rb_c, pb_c, gam, igm1, f);
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) FY(q, fi, cx) = f[q];
-                }
-            }
-            if (p >= z0) {
-                T wlz[NV], wrz[NV];
-                z_states(wlz, wrz);
-                hllc<T, ND, 2, HSE>(wlz, wrz, rb_f, pb_f, gam, igm1, fz);
-            } else {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) fz[q] = T(0);
-            }
-        } else if (xy) {
+        if (xy) {
             T wlx[NV], wrx[NV], wly[NV], wry[NV], wlz[NV], wrz[NV], fxv[NV], fyv[NV];
             // the low face of this cell is a wall when it sits on the domain's
             // low boundary, or on the high boundary (ragged tile: the cell is
