@@ -411,11 +411,18 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     auto DY = [&](int pz, int q, int f, int cx) -> T & {   // f in [-2, TY], cx in [-1, TX]
         return dif[(pz & 1) * (S::dxn + S::dyn) + S::dxn + (q * (TY + 3) + f + 2) * DYR + cx + 1];
     };
+    // Each SM sub-partition (warp mod 4) has its own FP64 unit.  The ring
+    // cells' half steps run on warps 2 and 3 (ring_start below), so the
+    // differences are formed by warps 0, 1, 4, 5, ... (those with warp mod 4
+    // < 2): the four units then carry about the same FP64 work between the
+    // barriers.
+    static_assert(!DIFFS || NT % 128 == 0, "differences on half of the warps");
+    constexpr int NDT = NT / 2;
+    const int dlane = ((tid >> 7) << 6) + (tid & 63);   // index among the difference threads
     auto form_diffs = [&](int pz) {
         const int sl = (pz + 2 * NR) % NR;
-        // (the items past the second pass land on warps 2, 3, ...: warps 0
-        // and 1 hold the ring cells' half steps)
-        for (int i = rotated_start<NT>(tid); i < NDX + NDY; i += NT) {
+        if (tid & 64) return;
+        for (int i = dlane; i < NDX + NDY; i += NDT) {
             if (i < NDX) {
                 const int cy = i / DXR - 1, f = i % DXR - 2;
 #pragma unroll
@@ -618,7 +625,9 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
             // ring cells: x = -1 and x = TX (rows 0..TY-1), y = -1 and y = TY
             // (columns 0..TX-1); only their face toward the tile is needed
             constexpr int NRING = 2 * TY + 2 * TX;
-            for (int i = tid; i < NRING; i += NT) {
+            // (FP64: from warp 2 on, see form_diffs)
+            const int ring_start = DIFFS ? rotated_start<NT>(tid) : tid;
+            for (int i = ring_start; i < NRING; i += NT) {
                 int cx, cy;
                 bool xside;
                 if (i < 2 * TY) { xside = true; cy = i >> 1; cx = (i & 1) ? TX : -1; }
