@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "hydro_device.cuh"
+#include "per_device.h"
 
 // Staging depth (template argument AS): with AS the next plane is staged by
 // asynchronous global->shared copies (cp.async) issued one plane ahead, so
@@ -142,7 +143,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // One CTA's share of a step: tile `tile` (row-major over tiles_x) of the x-y
-// plane, z planes [chunk*zchunk, min((chunk+1)*zchunk, nz)), time step dtd.
+// plane, z planes [z0, z1), time step dtd.
 // On return smax/bad hold this thread's max CFL signal speed and whether one
 // of its new cells failed the admissibility check.
 // ST selects the update (STAGE_*): the MUSCL-Hancock step; the first
@@ -155,7 +156,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // zero, are left out (their FP64 additions of zeros are not folded).
 template <typename T, bool HSE, int TX, int TY, int ST = STAGE_HANCOCK, int RC = RECON_PLM,
           bool AS = (sizeof(T) == 8), bool GZ = false>
-__device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chunk, double dtd,
+__device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int z0, int z1, double dtd,
                                             unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
@@ -182,8 +183,6 @@ __device__ __forceinline__ void step3d_body(const StepArgs &a, int tile, int chu
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = (tile / a.tiles_x) * TY;
-    const int z0 = chunk * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, nz);
     const T *__restrict__ U = static_cast<const T *>(a.U);
     const T *__restrict__ U0 = static_cast<const T *>(a.U0);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
@@ -866,9 +865,36 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
     // moves; the host finds the current buffer from the step count
     if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) return;
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
-    T smax;
-    bool bad;
-    step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    T smax = T(0);
+    bool bad = false;
+    // The CTA's plane-tiles [L, L1) of the W = tiles x nz, taken tile by
+    // tile (one call site of the body for both grids).  Chunked grid:
+    // blockIdx = (tile, z-chunk), one column piece.  Balanced grid (one CTA
+    // per resident slot): CTA b marches [b W / G, (b + 1) W / G) -- the end of
+    // one tile's column and the start of the next -- so every CTA has the same
+    // number of planes and the launch has no partial last wave.
+    const int nz = a.n[2];
+    long long L, L1;
+    if (a.zchunk > 0) {
+        const int z0 = chunk * a.zchunk;
+        L = (long long)tile * nz + z0;
+        L1 = L + min(a.zchunk, nz - z0);
+    } else {
+        const long long W = (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY) * nz;
+        L = W * blockIdx.x / gridDim.x;
+        L1 = W * (blockIdx.x + 1) / gridDim.x;
+    }
+    while (L < L1) {
+        const int t = static_cast<int>(L / nz), z0 = static_cast<int>(L % nz);
+        const int z1 = static_cast<int>(min(static_cast<long long>(nz), z0 + (L1 - L)));
+        T sm;
+        bool bd;
+        step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, t, z0, z1, dtd, smem_raw, sm, bd);
+        smax = max_t(smax, sm);
+        bad = bad || bd;
+        L += z1 - z0;
+        if (L < L1) __syncthreads();   // the next column piece reuses the shared-memory ring
+    }
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
         // the intermediate state only raises error bits; dt and time move
@@ -911,7 +937,9 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, BatchQueue *q, int pari
             const double dtd = (dt_cfl >= sa.t_end - t_now) ? sa.t_end - t_now : dt_cfl;
             T smax;
             bool bad;
-            step3d_body<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS>(sa, w.tile, w.chunk, dtd, smem_raw, smax,
+            const int z0 = w.chunk * sa.zchunk;
+            step3d_body<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS>(sa, w.tile, z0, min(z0 + sa.zchunk, sa.n[2]),
+                                                                      dtd, smem_raw, smax,
                                                                       bad);
             const bool bad_cta = __syncthreads_or(bad) != 0;
             const double m = block_max_t<NT, T>(smax, red);
@@ -919,6 +947,32 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, BatchQueue *q, int pari
         }
         __syncthreads();
     }
+}
+
+// Launch of a single-solve step kernel k (TX x TY threads, smem bytes of
+// dynamic shared memory).  a.zchunk > 0: the chunked grid `grid` (tiles x
+// z-chunks).  a.zchunk == 0: the balanced grid -- as many CTAs as the device
+// holds resident at once (at most one per plane-tile), each marching an
+// equal share of the plane-tiles.  `once` and `resident` are the kernel's
+// own per-device set-up records.
+template <int TX, int TY, typename K>
+cudaError_t launch_step_grid(K k, size_t smem, PerDeviceOnce &once, PerDeviceInt &resident, const StepArgs &a,
+                             dim3 grid, cudaStream_t s)
+{
+    cudaError_t e;
+    if (a.zchunk > 0) {
+        e = ensure_smem_limit(once, k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, TX * TY, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    int g = 0;
+    e = persistent_grid(resident, k, smem, TX * TY, &g);
+    if (e != cudaSuccess) return e;
+    const long long W = (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY) * a.n[2];
+    if (g > W) g = static_cast<int>(W);
+    k<<<g, TX * TY, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace hydro

@@ -15,10 +15,8 @@ cudaError_t launch3d_g(const StepArgs &a, dim3 grid, cudaStream_t s)
     auto k = step3d_kernel<T, HSE, TX, TY, STAGE_HANCOCK, RECON_PLM, AS, GZ>;
     constexpr size_t smem = Step3DSmem<T, HSE, TX, TY, RECON_PLM, AS>::bytes;
     static PerDeviceOnce configured;   // the attribute is per function and device
-    const cudaError_t e = ensure_smem_limit(configured, k, smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, TX * TY, smem, s>>>(a);
-    return cudaGetLastError();
+    static PerDeviceInt resident;      // balanced grid size, per device
+    return launch_step_grid<TX, TY>(k, smem, configured, resident, a, grid, s);
 }
 
 // Gravity along z only (always so with the hydrostatic background) takes the

@@ -520,6 +520,8 @@ def hydro_batch_variant_shape(v: int):
 
 # paired-cell FP32 MUSCL-Hancock tile variants of single 3D solves
 PAIR_VARIANTS = (8, 9, 10)
+# hydro_set_zchunk: the balanced grid instead of z-chunks
+ZCHUNK_BALANCED = -1
 
 
 def tile_shape(variant: int):

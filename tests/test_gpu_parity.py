@@ -396,6 +396,41 @@ def test_tile_shape_invariance_bitwise(hy, prec, variants):
         sim.close()
 
 
+@pytest.mark.parametrize("prec,variants", [(inputs.FP64, (0, 1, 2, 6)), (inputs.FP32, (0, 3, 5, 7))])
+@pytest.mark.parametrize("scheme", [inputs.HANCOCK, inputs.SSPRK2], ids=["hancock", "rk2"])
+def test_balanced_grid_equals_chunked_grid_bitwise(hy, prec, variants, scheme):
+    """The balanced grid (z-chunk -1: every resident CTA marches an equal
+    share of the plane-tiles, across column boundaries) gives the bits of the
+    chunked grid.  On 37 x 37 x 45 cells a CTA's share is a few planes, so
+    shares start and end inside columns, at the bottom and at the top."""
+    prob, W = inputs.rayleigh_taylor(37, nz=45, amplitude=0.05, hse_subtract=1, precision=prec)
+    prob = prob.replace(n=(37, 37, 45), scheme=scheme)
+    for v in variants:
+        outs = []
+        for z in (7, hy.ZCHUNK_BALANCED):
+            sim = hy.Simulation(prob, W)
+            sim.configure(v, z)
+            sim.run_steps(4)
+            outs.append((sim.get_state(), sim.t, sim.dt))
+            sim.close()
+        assert np.array_equal(outs[0][0], outs[1][0]), v
+        assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2], v
+
+
+def test_balanced_grid_rejected_where_unsupported(hy):
+    prob, W = inputs.rayleigh_taylor(16, nz=16, amplitude=0.05, precision=inputs.FP32)
+    sim = hy.Simulation(prob, W)
+    sim.set_tile(8)                       # paired-cell kernel: z-chunks only
+    with pytest.raises(hy.HydroError):
+        sim.set_zchunk(hy.ZCHUNK_BALANCED)
+    sim.close()
+    prob2, W2 = inputs.kelvin_helmholtz(32, ndim=2, precision=inputs.FP64)
+    sim = hy.Simulation(prob2, W2)
+    with pytest.raises(hy.HydroError):
+        sim.set_zchunk(hy.ZCHUNK_BALANCED)
+    sim.close()
+
+
 @pytest.mark.parametrize("mode", ["fp64", "fp64_hse", "fp32_hse"])
 def test_init_from_conserved_matches_init_from_primitives(hy, orc, mode):
     """hydro_init_conserved with the total conserved variables of an initial
