@@ -1,7 +1,7 @@
 // ctu3d.cu -- FP64 and FP32 instantiations of the fused 3D corner transport
 // upwind step.  Tiles: FP32 16 x 16 (256 threads, 152 KB of shared memory),
-// FP64 16 x 8 (128 threads, 171 KB); z-chunks sized for several waves of
-// the 152 SMs (one CTA per SM).
+// FP64 16 x 8 (128 threads, 171 KB); FP32 z-chunks sized for several waves
+// of the 152 SMs (one CTA per SM), FP64 the balanced grid.
 #include <algorithm>
 
 #include "ctu3d.cuh"
@@ -29,14 +29,25 @@ cudaError_t launch_ctu(const StepArgs &a0, cudaStream_t s)
 {
     auto k = ctu3d_kernel<T, HSE, TX, TY>;
     constexpr size_t smem = Ctu3DSmem<T, TX, TY>::bytes;
-    static PerDeviceOnce configured;   // the attribute is per function and device
-    const cudaError_t e = ensure_smem_limit(configured, k, smem);
+    static PerDeviceInt resident;   // resident CTAs of the balanced grid, per device
+    int g = 0;
+    const cudaError_t e = persistent_grid(resident, k, smem, TX * TY, &g);
     if (e != cudaSuccess) return e;
     StepArgs a = a0;
     a.tiles_x = (a.n[0] + TX - 1) / TX;
-    a.zchunk = ctu_zchunk(a.n, sizeof(T) == 4);
-    const dim3 grid(a.tiles_x * ((a.n[1] + TY - 1) / TY), (a.n[2] + a.zchunk - 1) / a.zchunk);
-    k<<<grid, TX * TY, smem, s>>>(a);
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the balanced grid, every resident CTA marching an equal share
+        // of the plane-tiles (no partial last wave; measured +8 % at RT 256^3).
+        // FP32 keeps z-chunks: the same speed there, and neighbouring tiles
+        // marched at the same heights keep their halo rows in L2
+        a.zchunk = 0;
+        const long long W = (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY) * a.n[2];
+        k<<<(int)std::min<long long>(g, W), TX * TY, smem, s>>>(a);
+    } else {
+        a.zchunk = ctu_zchunk(a.n, sizeof(T) == 4);
+        const dim3 grid(a.tiles_x * ((a.n[1] + TY - 1) / TY), (a.n[2] + a.zchunk - 1) / a.zchunk);
+        k<<<grid, TX * TY, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

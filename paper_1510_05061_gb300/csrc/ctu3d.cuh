@@ -123,7 +123,7 @@ __device__ __forceinline__ void predict_axis_bg(const T (&w)[5], const T (&dwd)[
 }
 
 template <typename T, bool HSE, int TX, int TY>
-__device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chunk, double dtd,
+__device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int z0, int z1, double dtd,
                                            unsigned char *smem_raw, T &smax, bool &bad)
 {
     constexpr int ND = 3, NV = 5, NT = TX * TY;
@@ -139,8 +139,6 @@ __device__ __forceinline__ void ctu3d_body(const StepArgs &a, int tile, int chun
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = (tile % a.tiles_x) * TX;
     const int y0 = (tile / a.tiles_x) * TY;
-    const int z0 = chunk * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, nz);
     const T *__restrict__ U = static_cast<const T *>(a.U);
     T *__restrict__ Un = static_cast<T *>(a.Unew);
     const PlaneBGT<T> *bgT = static_cast<const PlaneBGT<T> *>(a.bgT);
@@ -537,9 +535,39 @@ __global__ void __launch_bounds__(TX * TY) ctu3d_kernel(const StepArgs a)
     // frozen: nothing moves (the host finds the current buffer from the step count)
     if (t_now >= a.t_end || a.ctrl->err != 0 || a.ctrl->step >= a.step_end) return;
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
-    T smax;
-    bool bad;
-    ctu3d_body<T, HSE, TX, TY>(a, tile, chunk, dtd, smem_raw, smax, bad);
+    T smax = T(0);
+    bool bad = false;
+    // the CTA's plane-tiles [L, L1) of the W = tiles x nz, tile by tile:
+    // one z-chunk of one tile (a.zchunk > 0), or an equal share of all of
+    // them (a.zchunk == 0, the balanced grid of the MUSCL-Hancock step)
+    const int nz = a.n[2];
+    long long L, L1;
+    if (a.zchunk > 0) {
+        const int z0 = chunk * a.zchunk;
+        L = (long long)tile * nz + z0;
+        L1 = L + min(a.zchunk, nz - z0);
+    } else {
+        const long long W = (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY) * nz;
+        L = W * blockIdx.x / gridDim.x;
+        L1 = W * (blockIdx.x + 1) / gridDim.x;
+    }
+    // The pieces are marched from the last one back: the piece that starts
+    // at z = 0 (the head of the range's last column) first, the tail of its
+    // first column last.  Every CTA then marches height z at time z in its
+    // first piece and at time z + (share - nz) in its second, so neighbouring
+    // tiles are at one of two heights at a time instead of any height.
+    while (L1 > L) {
+        const long long t = (L1 - 1) / nz;
+        const long long Lt = max(L, t * nz);
+        const int z0 = static_cast<int>(Lt - t * nz), z1 = static_cast<int>(L1 - t * nz);
+        T sm;
+        bool bd;
+        ctu3d_body<T, HSE, TX, TY>(a, static_cast<int>(t), z0, z1, dtd, smem_raw, sm, bd);
+        smax = max_t(smax, sm);
+        bad = bad || bd;
+        L1 = Lt;
+        if (L1 > L) __syncthreads();   // the next column piece reuses the shared-memory ring
+    }
     const bool bad_cta = __syncthreads_or(bad) != 0;
     const double m = block_max_t<NT, T>(smax, red);
     finish_step<NT>(m, bad_cta, a, gridDim.x * gridDim.y, blockIdx.x + blockIdx.y * gridDim.x, dtd, true,

@@ -884,16 +884,22 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
         L = W * blockIdx.x / gridDim.x;
         L1 = W * (blockIdx.x + 1) / gridDim.x;
     }
-    while (L < L1) {
-        const int t = static_cast<int>(L / nz), z0 = static_cast<int>(L % nz);
-        const int z1 = static_cast<int>(min(static_cast<long long>(nz), z0 + (L1 - L)));
+    // The pieces are marched from the last one back: the piece that starts
+    // at z = 0 (the head of the range's last column) first, the tail of its
+    // first column last.  Every CTA then marches height z at time z in its
+    // first piece and at time z + (share - nz) in its second, so neighbouring
+    // tiles are at one of two heights at a time instead of any height.
+    while (L1 > L) {
+        const long long t = (L1 - 1) / nz;
+        const long long Lt = max(L, t * nz);
+        const int z0 = static_cast<int>(Lt - t * nz), z1 = static_cast<int>(L1 - t * nz);
         T sm;
         bool bd;
-        step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, t, z0, z1, dtd, smem_raw, sm, bd);
+        step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, static_cast<int>(t), z0, z1, dtd, smem_raw, sm, bd);
         smax = max_t(smax, sm);
         bad = bad || bd;
-        L += z1 - z0;
-        if (L < L1) __syncthreads();   // the next column piece reuses the shared-memory ring
+        L1 = Lt;
+        if (L1 > L) __syncthreads();   // the next column piece reuses the shared-memory ring
     }
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
