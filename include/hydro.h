@@ -422,7 +422,8 @@ int hydro_slabs_exchange_plan(const hydro_problem *global, int nranks, int *out,
 int hydro_slabs_init(const hydro_problem *global, int nranks, void *const *Ua, void *const *Ub,
                      void *const *work, const double *W0, const double *bg, void *stream,
                      hydro_slabs **out);
-/* Choose the 3D tile shape and z-chunk (0: default) of the slabs' steps. */
+/* Choose the 3D tile shape and z-chunk (0: default; HYDRO_ZCHUNK_BALANCED:
+   each slab's step on the balanced grid) of the slabs' steps. */
 int hydro_slabs_configure(hydro_slabs *s, int variant, int zchunk);
 /* Enqueue nsteps full steps (exchange, R step kernels, dt reduction each).
    The R step kernels run concurrently on internal streams forked from and

@@ -141,6 +141,7 @@ __global__ void dt_allreduce_kernel(Ctrl **ctrls, int R, double cfl)
 struct hydro_slabs {
     hydro_problem g;
     int R, nvar, cur, variant, zchunk;
+    bool balanced;   // the balanced grid instead of z-chunks (HYDRO_ZCHUNK_BALANCED)
     size_t bytes_per;              // value size
     long long plane;
     std::vector<Slab> slab;
@@ -186,7 +187,7 @@ StepArgs slab_args(const hydro_slabs *S, const Slab &sl)
     a.bgT = nullptr;
     if (S->g.hse_subtract)
         a.bgT = S->g.precision == HYDRO_FP32 ? static_cast<const void *>(sl.bgf) : static_cast<const void *>(sl.bg);
-    a.zchunk = std::min(S->zchunk, sl.nz);
+    a.zchunk = S->balanced ? 0 : std::min(S->zchunk, sl.nz);   // 0: balanced grid
     a.tiles_x = sl.tiles_x;
     fill_fp32_constants(a);
     return a;
@@ -430,7 +431,8 @@ int hydro_slabs_step(hydro_slabs *S, long nsteps)
         for (int r = 0; r < S->R && e == cudaSuccess; ++r) {
             const Slab &sl = S->slab[r];
             StepArgs a = slab_args(S, sl);
-            const int nch = (sl.nz + a.zchunk - 1) / a.zchunk;
+            // (the balanced grid's size is the launcher's)
+            const int nch = a.zchunk > 0 ? (sl.nz + a.zchunk - 1) / a.zchunk : 1;
             dim3 grid(sl.tiles_x * sl.tiles_y, nch);
             e = cudaStreamWaitEvent(S->side[r], S->fork, 0);
             if (e == cudaSuccess)
@@ -519,9 +521,11 @@ int hydro_slabs_reduce(hydro_slabs *S, int what, double *out)
 
 int hydro_slabs_configure(hydro_slabs *S, int variant, int zchunk)
 {
-    if (!S || !tile3d_available(variant, S->g.precision == HYDRO_FP32) || zchunk < 0) return HYDRO_ERR_INVALID_ARG;
+    if (!S || !tile3d_available(variant, S->g.precision == HYDRO_FP32)) return HYDRO_ERR_INVALID_ARG;
+    if (zchunk < 0 && zchunk != HYDRO_ZCHUNK_BALANCED) return HYDRO_ERR_INVALID_ARG;
     S->variant = variant;
-    S->zchunk = zchunk == 0 ? 64 : zchunk;
+    S->balanced = zchunk == HYDRO_ZCHUNK_BALANCED;
+    if (!S->balanced) S->zchunk = zchunk == 0 ? 64 : zchunk;
     for (Slab &sl : S->slab) {
         sl.tiles_x = tiles_along(S->g.n[0], TILE3D_SHAPES[variant].tx);
         sl.tiles_y = tiles_along(S->g.n[1], TILE3D_SHAPES[variant].ty);
