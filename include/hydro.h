@@ -184,13 +184,16 @@ int hydro_get_fields(hydro_sim *sim, int what, double *host_dst);
 int hydro_debug_poke(hydro_sim *sim, int var, long cell, double v);
 
 /* Select the 3D z-chunk length (planes per CTA); 0 restores the default.
-   HYDRO_ZCHUNK_BALANCED instead launches the balanced grid: as many CTAs
-   as the device holds resident at once, each marching an equal share of
-   the (tile, plane) pairs taken tile by tile, so that the launch has no
-   partial last wave (MUSCL-Hancock and SSP-RK2 steps of tile variants
-   0..7; HYDRO_ERR_INVALID_ARG for 2D, the corner transport upwind step and
-   the paired-cell variants, and selecting a paired-cell variant returns to
-   z-chunks).  Results do not depend on the choice. */
+   A negative value selects the balanced grid instead: as many CTAs as the
+   device holds resident at once, the (tile, z-chunk) pieces taken in whole
+   waves of neighbouring tiles at the same heights while at least one wave
+   remains, and the planes of the last, partial wave split evenly, so that
+   every CTA marches the same number of planes and the launch has no partial
+   last wave.  HYDRO_ZCHUNK_BALANCED (-1) uses whole columns as the pieces,
+   -Z pieces of Z planes.  MUSCL-Hancock and SSP-RK2 steps of tile variants
+   0..7 only: HYDRO_ERR_INVALID_ARG for 2D, the corner transport upwind step
+   and the paired-cell variants, and selecting a paired-cell variant returns
+   to z-chunks.  Results do not depend on the choice. */
 #define HYDRO_ZCHUNK_BALANCED (-1)
 int hydro_set_zchunk(hydro_sim *sim, int zchunk);
 

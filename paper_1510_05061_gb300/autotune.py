@@ -161,11 +161,12 @@ def time_sim_steps(sim, steps: int) -> float:
     return a.elapsed_time(b) / steps
 
 
-def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 128, -1),
+def tune_simulation(sim, steps: int = 3, zchunks: Iterable[int] = (16, 32, 64, 128, -1, -64, -128),
                     variants: Optional[Iterable[int]] = None, use_cache: bool = True) -> dict:
     """Configure a single 3D solve with its fastest (tile shape, z-chunk);
-    z-chunk -1 is the balanced grid (hydro.ZCHUNK_BALANCED).  Tuning advances
-    the solve by the steps it times."""
+    a negative z-chunk is the balanced grid (-1, hydro.ZCHUNK_BALANCED: over
+    whole columns; -Z: over Z-plane chunks).  Tuning advances the solve by the
+    steps it times."""
     from . import hydro
 
     if sim.prob.ndim != 3 or getattr(sim.prob, "scheme", 0) == inputs.CTU:

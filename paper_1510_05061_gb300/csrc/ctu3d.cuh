@@ -537,36 +537,19 @@ __global__ void __launch_bounds__(TX * TY) ctu3d_kernel(const StepArgs a)
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax = T(0);
     bool bad = false;
-    // the CTA's plane-tiles [L, L1) of the W = tiles x nz, tile by tile:
-    // one z-chunk of one tile (a.zchunk > 0), or an equal share of all of
-    // them (a.zchunk == 0, the balanced grid of the MUSCL-Hancock step)
-    const int nz = a.n[2];
-    long long L, L1;
-    if (a.zchunk > 0) {
-        const int z0 = chunk * a.zchunk;
-        L = (long long)tile * nz + z0;
-        L1 = L + min(a.zchunk, nz - z0);
-    } else {
-        const long long W = (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY) * nz;
-        L = W * blockIdx.x / gridDim.x;
-        L1 = W * (blockIdx.x + 1) / gridDim.x;
-    }
-    // The pieces are marched from the last one back: the piece that starts
-    // at z = 0 (the head of the range's last column) first, the tail of its
-    // first column last.  Every CTA then marches height z at time z in its
-    // first piece and at time z + (share - nz) in its second, so neighbouring
-    // tiles are at one of two heights at a time instead of any height.
-    while (L1 > L) {
-        const long long t = (L1 - 1) / nz;
-        const long long Lt = max(L, t * nz);
-        const int z0 = static_cast<int>(Lt - t * nz), z1 = static_cast<int>(L1 - t * nz);
+    // the CTA's column pieces: one z-chunk of one tile (chunked grid), or
+    // its share of the balanced grid (PieceIter)
+    PieceIter pieces(a.zchunk, (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY), a.n[2], tile, chunk);
+    int t, z0, z1;
+    bool first = true;
+    while (pieces.next(t, z0, z1)) {
+        if (!first) __syncthreads();   // the next piece reuses the shared-memory ring
+        first = false;
         T sm;
         bool bd;
-        ctu3d_body<T, HSE, TX, TY>(a, static_cast<int>(t), z0, z1, dtd, smem_raw, sm, bd);
+        ctu3d_body<T, HSE, TX, TY>(a, t, z0, z1, dtd, smem_raw, sm, bd);
         smax = max_t(smax, sm);
         bad = bad || bd;
-        L1 = Lt;
-        if (L1 > L) __syncthreads();   // the next column piece reuses the shared-memory ring
     }
     const bool bad_cta = __syncthreads_or(bad) != 0;
     const double m = block_max_t<NT, T>(smax, red);

@@ -42,7 +42,7 @@ struct hydro_sim {
     int tiles_x, tiles_y;
     int variant;             // 3D tile shape (TILE3D_SHAPES index)
     int zchunk;
-    bool balanced;           // 3D: balanced grid instead of z-chunks (HYDRO_ZCHUNK_BALANCED)
+    int balanced;            // 3D: 0, or the balanced grid's z-chunk setting (-1: whole columns, -Z)
     long launches;
     int err_state;           // sticky host-side copy of a non-physical error
     std::vector<PlaneBG> bg_host;
@@ -242,7 +242,7 @@ StepArgs step_args(const hydro_sim *s, double t_end)
         a.bgT = s->prob.precision == HYDRO_FP32 ? static_cast<const void *>(s->bgf)
                                                 : static_cast<const void *>(s->bg);
     a.U0 = nullptr;
-    a.zchunk = s->balanced ? 0 : s->zchunk;   // 0: balanced grid
+    a.zchunk = s->balanced ? s->balanced : s->zchunk;   // <= 0: balanced grid
     a.tiles_x = s->tiles_x;
     fill_fp32_constants(a);
     return a;
@@ -619,17 +619,18 @@ int hydro_debug_poke(hydro_sim *s, int var, long cell, double v)
 int hydro_set_zchunk(hydro_sim *s, int zchunk)
 {
     if (!s) return HYDRO_ERR_INVALID_ARG;
-    if (zchunk == HYDRO_ZCHUNK_BALANCED) {
-        // 3D MUSCL-Hancock and SSP-RK2 kernels of tile variants 0..7 only
+    if (zchunk < 0) {
+        // the balanced grid (HYDRO_ZCHUNK_BALANCED: over whole columns; -Z:
+        // over Z-plane chunks): 3D MUSCL-Hancock and SSP-RK2 kernels of tile
+        // variants 0..7 only
         if (s->prob.ndim != 3 || s->prob.scheme == HYDRO_SCHEME_CTU || pair_variant(s->variant))
             return HYDRO_ERR_INVALID_ARG;
-        s->balanced = true;
+        s->balanced = zchunk;
         return HYDRO_OK;
     }
-    if (zchunk < 0) return HYDRO_ERR_INVALID_ARG;
     if (s->prob.ndim == 2) return zchunk <= 1 ? HYDRO_OK : HYDRO_ERR_INVALID_ARG;
     s->zchunk = zchunk == 0 ? default_zchunk(s) : std::min(zchunk, s->prob.n[2]);
-    s->balanced = false;
+    s->balanced = 0;
     return HYDRO_OK;
 }
 
@@ -647,7 +648,7 @@ int hydro_set_tile(hydro_sim *s, int variant)
     // the other integrators take only the shape of variants 0..7
     if (s->prob.scheme != HYDRO_SCHEME_HANCOCK && pair_variant(variant)) return HYDRO_ERR_INVALID_ARG;
     s->variant = variant;
-    if (pair_variant(variant)) s->balanced = false;   // the paired kernel has z-chunks only
+    if (pair_variant(variant)) s->balanced = 0;   // the paired kernel has z-chunks only
     s->tiles_x = tiles_along(s->prob.n[0], tile_shape(variant).tx);
     s->tiles_y = tiles_along(s->prob.n[1], tile_shape(variant).ty);
     return HYDRO_OK;

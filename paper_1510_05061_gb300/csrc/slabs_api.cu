@@ -141,7 +141,7 @@ __global__ void dt_allreduce_kernel(Ctrl **ctrls, int R, double cfl)
 struct hydro_slabs {
     hydro_problem g;
     int R, nvar, cur, variant, zchunk;
-    bool balanced;   // the balanced grid instead of z-chunks (HYDRO_ZCHUNK_BALANCED)
+    int balanced;    // 0, or the balanced grid's z-chunk setting (-1: whole columns, -Z)
     size_t bytes_per;              // value size
     long long plane;
     std::vector<Slab> slab;
@@ -187,7 +187,7 @@ StepArgs slab_args(const hydro_slabs *S, const Slab &sl)
     a.bgT = nullptr;
     if (S->g.hse_subtract)
         a.bgT = S->g.precision == HYDRO_FP32 ? static_cast<const void *>(sl.bgf) : static_cast<const void *>(sl.bg);
-    a.zchunk = S->balanced ? 0 : std::min(S->zchunk, sl.nz);   // 0: balanced grid
+    a.zchunk = S->balanced ? S->balanced : std::min(S->zchunk, sl.nz);   // <= 0: balanced grid
     a.tiles_x = sl.tiles_x;
     fill_fp32_constants(a);
     return a;
@@ -522,9 +522,8 @@ int hydro_slabs_reduce(hydro_slabs *S, int what, double *out)
 int hydro_slabs_configure(hydro_slabs *S, int variant, int zchunk)
 {
     if (!S || !tile3d_available(variant, S->g.precision == HYDRO_FP32)) return HYDRO_ERR_INVALID_ARG;
-    if (zchunk < 0 && zchunk != HYDRO_ZCHUNK_BALANCED) return HYDRO_ERR_INVALID_ARG;
     S->variant = variant;
-    S->balanced = zchunk == HYDRO_ZCHUNK_BALANCED;
+    S->balanced = zchunk < 0 ? zchunk : 0;
     if (!S->balanced) S->zchunk = zchunk == 0 ? 64 : zchunk;
     for (Slab &sl : S->slab) {
         sl.tiles_x = tiles_along(S->g.n[0], TILE3D_SHAPES[variant].tx);

@@ -867,39 +867,19 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
     const double dtd = (dt_cfl >= a.t_end - t_now) ? a.t_end - t_now : dt_cfl;
     T smax = T(0);
     bool bad = false;
-    // The CTA's plane-tiles [L, L1) of the W = tiles x nz, taken tile by
-    // tile (one call site of the body for both grids).  Chunked grid:
-    // blockIdx = (tile, z-chunk), one column piece.  Balanced grid (one CTA
-    // per resident slot): CTA b marches [b W / G, (b + 1) W / G) -- the end of
-    // one tile's column and the start of the next -- so every CTA has the same
-    // number of planes and the launch has no partial last wave.
-    const int nz = a.n[2];
-    long long L, L1;
-    if (a.zchunk > 0) {
-        const int z0 = chunk * a.zchunk;
-        L = (long long)tile * nz + z0;
-        L1 = L + min(a.zchunk, nz - z0);
-    } else {
-        const long long W = (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY) * nz;
-        L = W * blockIdx.x / gridDim.x;
-        L1 = W * (blockIdx.x + 1) / gridDim.x;
-    }
-    // The pieces are marched from the last one back: the piece that starts
-    // at z = 0 (the head of the range's last column) first, the tail of its
-    // first column last.  Every CTA then marches height z at time z in its
-    // first piece and at time z + (share - nz) in its second, so neighbouring
-    // tiles are at one of two heights at a time instead of any height.
-    while (L1 > L) {
-        const long long t = (L1 - 1) / nz;
-        const long long Lt = max(L, t * nz);
-        const int z0 = static_cast<int>(Lt - t * nz), z1 = static_cast<int>(L1 - t * nz);
+    // the CTA's column pieces: one z-chunk of one tile (chunked grid), or
+    // its share of the balanced grid (PieceIter)
+    PieceIter pieces(a.zchunk, (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY), a.n[2], tile, chunk);
+    int t, z0, z1;
+    bool first = true;
+    while (pieces.next(t, z0, z1)) {
+        if (!first) __syncthreads();   // the next piece reuses the shared-memory ring
+        first = false;
         T sm;
         bool bd;
-        step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, static_cast<int>(t), z0, z1, dtd, smem_raw, sm, bd);
+        step3d_body<T, HSE, TX, TY, ST, RC, AS, GZ>(a, t, z0, z1, dtd, smem_raw, sm, bd);
         smax = max_t(smax, sm);
         bad = bad || bd;
-        L1 = Lt;
-        if (L1 > L) __syncthreads();   // the next column piece reuses the shared-memory ring
     }
     const bool bad_cta = __syncthreads_or(bad) != 0;
     if constexpr (ST == STAGE_RK1) {
@@ -957,10 +937,9 @@ step3d_batch_kernel(const BatchInst *__restrict__ insts, BatchQueue *q, int pari
 
 // Launch of a single-solve step kernel k (TX x TY threads, smem bytes of
 // dynamic shared memory).  a.zchunk > 0: the chunked grid `grid` (tiles x
-// z-chunks).  a.zchunk == 0: the balanced grid -- as many CTAs as the device
-// holds resident at once (at most one per plane-tile), each marching an
-// equal share of the plane-tiles.  `once` and `resident` are the kernel's
-// own per-device set-up records.
+// z-chunks).  a.zchunk <= 0: the balanced grid (PieceIter) -- as many CTAs as
+// the device holds resident at once, at most one per plane-tile.  `once`
+// and `resident` are the kernel's own per-device set-up records.
 template <int TX, int TY, typename K>
 cudaError_t launch_step_grid(K k, size_t smem, PerDeviceOnce &once, PerDeviceInt &resident, const StepArgs &a,
                              dim3 grid, cudaStream_t s)

@@ -399,22 +399,24 @@ def test_tile_shape_invariance_bitwise(hy, prec, variants):
 @pytest.mark.parametrize("prec,variants", [(inputs.FP64, (0, 1, 2, 6)), (inputs.FP32, (0, 3, 5, 7))])
 @pytest.mark.parametrize("scheme", [inputs.HANCOCK, inputs.SSPRK2], ids=["hancock", "rk2"])
 def test_balanced_grid_equals_chunked_grid_bitwise(hy, prec, variants, scheme):
-    """The balanced grid (z-chunk -1: every resident CTA marches an equal
-    share of the plane-tiles, across column boundaries) gives the bits of the
-    chunked grid.  On 37 x 37 x 45 cells a CTA's share is a few planes, so
-    shares start and end inside columns, at the bottom and at the top."""
+    """The balanced grid (negative z-chunk: whole waves of chunks, then the
+    last wave's planes split evenly over every resident CTA) gives the bits of
+    the chunked grid: over whole columns (-1, -45), 5-plane chunks (45 = 9 x 5)
+    and 7-plane chunks (a 3-plane last row).  On 37 x 37 x 45 cells the split
+    pieces are a few planes long and begin and end inside chunks."""
     prob, W = inputs.rayleigh_taylor(37, nz=45, amplitude=0.05, hse_subtract=1, precision=prec)
     prob = prob.replace(n=(37, 37, 45), scheme=scheme)
     for v in variants:
         outs = []
-        for z in (7, hy.ZCHUNK_BALANCED):
+        for z in (7, hy.ZCHUNK_BALANCED, -5, -7, -45):
             sim = hy.Simulation(prob, W)
             sim.configure(v, z)
             sim.run_steps(4)
             outs.append((sim.get_state(), sim.t, sim.dt))
             sim.close()
-        assert np.array_equal(outs[0][0], outs[1][0]), v
-        assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2], v
+        for z, o in zip((hy.ZCHUNK_BALANCED, -5, -7, -45), outs[1:]):
+            assert np.array_equal(outs[0][0], o[0]), (v, z)
+            assert outs[0][1] == o[1] and outs[0][2] == o[2], (v, z)
 
 
 def test_balanced_grid_rejected_where_unsupported(hy):

@@ -91,7 +91,7 @@ def test_slabs_match_undivided(hy, name, R):
     assert_same(got, ref)
 
 
-@pytest.mark.parametrize("variant,zchunk", [(1, 3), (2, 0), (0, 1), (6, -1), (0, -1)])
+@pytest.mark.parametrize("variant,zchunk", [(1, 3), (2, 0), (0, 1), (6, -1), (0, -1), (2, -4)])
 def test_slabs_tile_and_chunk_invariance(hy, variant, zchunk):
     prob, W = rt(n=40, nz=30)
     ref = whole(hy, prob, W, 5)
