@@ -419,6 +419,25 @@ def test_balanced_grid_equals_chunked_grid_bitwise(hy, prec, variants, scheme):
             assert outs[0][1] == o[1] and outs[0][2] == o[2], (v, z)
 
 
+@pytest.mark.parametrize("prec,variant", [(inputs.FP64, 6), (inputs.FP64, 2), (inputs.FP32, 0), (inputs.FP32, 3)])
+def test_balanced_grid_whole_waves_bitwise(hy, prec, variant):
+    """A grid with more chunks than resident CTAs, so that the balanced grid
+    takes whole waves of chunks before splitting the last one (128 x 128 x 64
+    cells; 4- and 8-plane chunks give 16 and 8 chunks per column), gives the
+    bits of the chunked grid."""
+    prob, W = inputs.rayleigh_taylor(128, nz=64, amplitude=0.05, hse_subtract=1, precision=prec)
+    outs = []
+    for z in (16, -4, -8, hy.ZCHUNK_BALANCED):
+        sim = hy.Simulation(prob, W)
+        sim.configure(variant, z)
+        sim.run_steps(3)
+        outs.append((sim.get_state(), sim.t, sim.dt))
+        sim.close()
+    for z, o in zip((-4, -8, hy.ZCHUNK_BALANCED), outs[1:]):
+        assert np.array_equal(outs[0][0], o[0]), (variant, z)
+        assert outs[0][1] == o[1] and outs[0][2] == o[2], (variant, z)
+
+
 def test_balanced_grid_rejected_where_unsupported(hy):
     prob, W = inputs.rayleigh_taylor(16, nz=16, amplitude=0.05, precision=inputs.FP32)
     sim = hy.Simulation(prob, W)
