@@ -625,7 +625,7 @@ int hydro_set_zchunk(hydro_sim *s, int zchunk)
         // variants 0..7 only
         if (s->prob.ndim != 3 || s->prob.scheme == HYDRO_SCHEME_CTU || pair_variant(s->variant))
             return HYDRO_ERR_INVALID_ARG;
-        s->balanced = zchunk;
+        s->balanced = std::max(zchunk, -s->prob.n[2]);   // chunks of at most nz planes
         return HYDRO_OK;
     }
     if (s->prob.ndim == 2) return zchunk <= 1 ? HYDRO_OK : HYDRO_ERR_INVALID_ARG;

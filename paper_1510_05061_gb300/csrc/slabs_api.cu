@@ -523,7 +523,7 @@ int hydro_slabs_configure(hydro_slabs *S, int variant, int zchunk)
 {
     if (!S || !tile3d_available(variant, S->g.precision == HYDRO_FP32)) return HYDRO_ERR_INVALID_ARG;
     S->variant = variant;
-    S->balanced = zchunk < 0 ? zchunk : 0;
+    S->balanced = zchunk < 0 ? std::max(zchunk, -S->g.n[2]) : 0;   // chunks of at most nz planes
     if (!S->balanced) S->zchunk = zchunk == 0 ? 64 : zchunk;
     for (Slab &sl : S->slab) {
         sl.tiles_x = tiles_along(S->g.n[0], TILE3D_SHAPES[variant].tx);

@@ -427,13 +427,14 @@ def test_balanced_grid_whole_waves_bitwise(hy, prec, variant):
     bits of the chunked grid."""
     prob, W = inputs.rayleigh_taylor(128, nz=64, amplitude=0.05, hse_subtract=1, precision=prec)
     outs = []
-    for z in (16, -4, -8, hy.ZCHUNK_BALANCED):
+    # (-10**6: chunks longer than the column are whole columns)
+    for z in (16, -4, -8, hy.ZCHUNK_BALANCED, -10**6):
         sim = hy.Simulation(prob, W)
         sim.configure(variant, z)
         sim.run_steps(3)
         outs.append((sim.get_state(), sim.t, sim.dt))
         sim.close()
-    for z, o in zip((-4, -8, hy.ZCHUNK_BALANCED), outs[1:]):
+    for z, o in zip((-4, -8, hy.ZCHUNK_BALANCED, -10**6), outs[1:]):
         assert np.array_equal(outs[0][0], o[0]), (variant, z)
         assert outs[0][1] == o[1] and outs[0][2] == o[2], (variant, z)
 
