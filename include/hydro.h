@@ -229,6 +229,15 @@ long hydro_launch_count(hydro_sim *sim);
 int hydro_checkpoint_save(hydro_sim *sim, const char *path);
 int hydro_checkpoint_load(hydro_sim *sim, const char *path);
 
+/* Test hook, needs no GPU: the column pieces (tile, first plane, end plane)
+   one CTA of a 3D step marches, in marching order -- the chunked grid's CTA
+   (tile, chunk) for zchunk > 0, else CTA b of a balanced grid of G CTAs
+   (hydro_set_zchunk's negative settings) -- for `tiles` tiles of nz planes.
+   Writes up to max_pieces triples to out and returns the number of pieces,
+   or HYDRO_ERR_INVALID_ARG. */
+int hydro_debug_pieces(int zchunk, long long tiles, int nz, int tile, int chunk, long long G, long long b,
+                       int *out, int max_pieces);
+
 /* Test hook: evaluate the update's FP64 arithmetic helpers on n device
    values, out[i] = 1/x[i] (which = 0), y[i]/x[i] (1), 1/sqrt(x[i]) (2) or
    the MC-limited slope of (x[i], y[i]) (3), so that they can be checked

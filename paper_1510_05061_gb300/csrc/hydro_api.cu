@@ -18,6 +18,7 @@
 #include "hydro_internal.h"
 #include "launchers.h"
 #include "per_device.h"
+#include "pieces.h"
 
 using namespace hydro;
 
@@ -652,6 +653,26 @@ int hydro_set_tile(hydro_sim *s, int variant)
     s->tiles_x = tiles_along(s->prob.n[0], tile_shape(variant).tx);
     s->tiles_y = tiles_along(s->prob.n[1], tile_shape(variant).ty);
     return HYDRO_OK;
+}
+
+int hydro_debug_pieces(int zchunk, long long tiles, int nz, int tile, int chunk, long long G, long long b,
+                       int *out, int max_pieces)
+{
+    if (!out || tiles <= 0 || nz <= 0 || max_pieces < 0) return HYDRO_ERR_INVALID_ARG;
+    if (zchunk > 0 && (tile < 0 || tile >= tiles || chunk < 0 || (long long)chunk * zchunk >= nz))
+        return HYDRO_ERR_INVALID_ARG;
+    if (zchunk <= 0 && (G <= 0 || b < 0 || b >= G)) return HYDRO_ERR_INVALID_ARG;
+    PieceIter it(zchunk, tiles, nz, tile, chunk, G, b);
+    int n = 0, t, z0, z1;
+    while (it.next(t, z0, z1)) {
+        if (n < max_pieces) {
+            out[3 * n] = t;
+            out[3 * n + 1] = z0;
+            out[3 * n + 2] = z1;
+        }
+        ++n;
+    }
+    return n;
 }
 
 int hydro_tile_shape(int variant, int *tx, int *ty)

@@ -869,7 +869,8 @@ __global__ void __launch_bounds__(TX * TY, HYDRO_STEP3D_MIN_CTAS(T, TX, TY)) ste
     bool bad = false;
     // the CTA's column pieces: one z-chunk of one tile (chunked grid), or
     // its share of the balanced grid (PieceIter)
-    PieceIter pieces(a.zchunk, (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY), a.n[2], tile, chunk);
+    PieceIter pieces(a.zchunk, (long long)a.tiles_x * ((a.n[1] + TY - 1) / TY), a.n[2], tile, chunk,
+                     gridDim.x, blockIdx.x);
     int t, z0, z1;
     bool first = true;
     while (pieces.next(t, z0, z1)) {

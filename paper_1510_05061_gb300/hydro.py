@@ -43,7 +43,7 @@ HYDRO_RED_DT_LAST = 6
 EXPORTS = (
     "hydro_state_bytes", "hydro_workspace_bytes", "hydro_init", "hydro_init_conserved", "hydro_step",
     "hydro_advance_to", "hydro_reduce", "hydro_current", "hydro_get_state",
-    "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_set_zchunk", "hydro_set_tile",
+    "hydro_set_state", "hydro_get_fields", "hydro_debug_poke", "hydro_debug_pieces", "hydro_set_zchunk", "hydro_set_tile",
     "hydro_launch_count", "hydro_tile_shape", "hydro_destroy", "hydro_strerror", "hydro_totals_noalloc",
     "hydro_selftest_math", "hydro_selftest_device_once", "hydro_fma_probe", "hydro_fma_probe_flops", "hydro_batch_workspace_bytes", "hydro_batch_init",
     "hydro_instance_work_bytes", "hydro_problem_max_items", "hydro_batch_create_bytes",
@@ -123,6 +123,9 @@ def load(path: str = LIB_PATH):
     L.hydro_destroy.argtypes = [vp]
     L.hydro_strerror.restype = C.c_char_p
     L.hydro_strerror.argtypes = [C.c_int]
+    L.hydro_debug_pieces.restype = C.c_int
+    L.hydro_debug_pieces.argtypes = [C.c_int, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_longlong,
+                                     C.c_longlong, vp, C.c_int]
     L.hydro_selftest_math.restype = C.c_int
     L.hydro_selftest_math.argtypes = [C.c_int, vp, vp, vp, C.c_long, vp]
     L.hydro_fma_probe.restype = C.c_int
@@ -321,6 +324,22 @@ def hydro_set_state(h, src: np.ndarray, t: float, step: int):
 
 def hydro_get_fields(h, what: int, dst: np.ndarray):
     _check(load().hydro_get_fields(h, int(what), _dptr(dst)), "hydro_get_fields")
+
+
+def hydro_debug_pieces(zchunk: int, tiles: int, nz: int, tile: int = 0, chunk: int = 0, G: int = 1, b: int = 0):
+    """Column pieces (tile, z0, z1) one CTA of a 3D step marches, in order
+    (test hook; no GPU needed)."""
+    L = load()
+    buf = (C.c_int * 3 * 64)()
+    n = L.hydro_debug_pieces(int(zchunk), int(tiles), int(nz), int(tile), int(chunk), int(G), int(b),
+                             C.cast(buf, C.c_void_p), 64)
+    if n < 0:
+        _check(n, "hydro_debug_pieces")
+    if n > 64:
+        buf = (C.c_int * 3 * n)()
+        n = L.hydro_debug_pieces(int(zchunk), int(tiles), int(nz), int(tile), int(chunk), int(G), int(b),
+                                 C.cast(buf, C.c_void_p), n)
+    return [tuple(buf[i]) for i in range(n)]
 
 
 def hydro_debug_poke(h, var: int, cell: int, v: float):
