@@ -1037,7 +1037,8 @@ def main():
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-tune", action="store_true", help="default tile shape and z-chunk")
     ap.add_argument("--variant", type=int, default=None, help="single 3D solves: fixed tile variant (no tuning)")
-    ap.add_argument("--zchunk", type=int, default=0, help="with --variant: z-chunk (0 = default)")
+    ap.add_argument("--zchunk", type=int, default=0,
+                    help="with --variant: z-chunk (0 = default; negative: the balanced grid, -1 over whole columns)")
     ap.add_argument("--show-tuning", action="store_true", help="print the autotuner's timing table to stderr")
     ap.add_argument("--requests", type=int, default=200, help="served configs: number of requests")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served configs: HBM budget")
